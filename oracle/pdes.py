@@ -1,0 +1,262 @@
+"""Discrete residuals of the four benchmark PDEs (oracle; test infrastructure).
+
+Each problem maps a flat state x (field-major, then row-major y, x) to the
+spatial operator G(x). Every function works unchanged on complex arrays so
+that ``oracle.jvp`` can differentiate it by the complex step: branches test
+the real part only and no non-analytic function (abs, max) is applied to a
+quantity that carries a derivative.
+
+The nonlinear system of one implicit step is the theta-method residual of
+Eq. 2 (x^k the Newton iterate, x* = x^n the previous state),
+
+    F(x; b) = M(x) - theta * dt * G(x) - b,
+    b       = M(x^n) + (1 - theta) * dt * G(x^n),
+
+with M the identity except for the radiation problem, where the material
+unknown T enters through its energy a T^4. theta = 1/2 is the paper's
+Crank-Nicolson scheme (Sec. 3.2, App. A); theta = 1 is backward Euler. The
+Maxwell problem is a boundary-value problem: F(x) = G(x).
+"""
+from __future__ import annotations
+
+from dataclasses import dataclass, field
+
+import numpy as np
+
+
+def _lap5_periodic(u: np.ndarray, hx: float, hy: float) -> np.ndarray:
+    """Second-order 5-point Laplacian with periodic wrap; u has shape (ny, nx)."""
+    return ((np.roll(u, -1, axis=1) - 2.0 * u + np.roll(u, 1, axis=1)) / (hx * hx)
+            + (np.roll(u, -1, axis=0) - 2.0 * u + np.roll(u, 1, axis=0)) / (hy * hy))
+
+
+class _ThetaProblem:
+    """Shared theta-method plumbing (Eq. 2 with a one-step time scheme)."""
+
+    bvp = False
+    theta = 0.5
+    dt = 0.1
+
+    def M(self, x):
+        return x
+
+    def rhs(self, xn):
+        """b = M(x^n) + (1 - theta) dt G(x^n), the constant part of F."""
+        return self.M(xn) + (1.0 - self.theta) * self.dt * self.G(xn)
+
+    def residual(self, x, b):
+        """F(x; b) = M(x) - theta dt G(x) - b."""
+        if self.bvp:
+            return self.G(x)
+        return self.M(x) - self.theta * self.dt * self.G(x) - b
+
+
+@dataclass
+class Burgers1D(_ThetaProblem):
+    """1D viscous Burgers u_t + (u^2/2)_x = nu u_xx on the periodic unit line.
+
+    Cells x_i = i h, h = 1/N. Conservative upwind convection: the face flux
+    Phi_{i+1/2} takes u_i^2/2 when the face speed (u_i + u_{i+1})/2 is >= 0 and
+    u_{i+1}^2/2 otherwise (this is the Roe flux for Burgers); diffusion is the
+    3-point central second difference. The paper's Burgers benchmark is the
+    2D central-difference form (App. A, Burgers' Equation); this is the 1D
+    upwind variant of the benchmark configuration, with theta = 1.
+    """
+
+    N: int = 1024
+    nu: float = 1e-2
+    dt: float = 1e-3
+    theta: float = 1.0
+
+    @property
+    def n_unknowns(self) -> int:
+        return self.N
+
+    def G(self, u):
+        h = 1.0 / self.N
+        up = np.roll(u, -1)   # u_{i+1}
+        um = np.roll(u, 1)    # u_{i-1}
+        face_speed = (u + up).real
+        phi_p = np.where(face_speed >= 0.0, 0.5 * u * u, 0.5 * up * up)  # Phi_{i+1/2}
+        phi_m = np.roll(phi_p, 1)                                        # Phi_{i-1/2}
+        return -(phi_p - phi_m) / h + self.nu * (up - 2.0 * u + um) / (h * h)
+
+
+@dataclass
+class AllenCahn2D(_ThetaProblem):
+    """Allen-Cahn u_t = D lap u + u - u^3, periodic unit square, 5-point Laplacian.
+
+    The benchmark variant of the paper's reaction-diffusion problem
+    (Sec. 3.2; App. A, Nonlinear Reaction-Diffusion), which has the sink
+    -u^3 only; ``linear_coef`` = 1 adds the Allen-Cahn +u term and 0 recovers
+    the paper's form D lap u - u^3.
+    """
+
+    nx: int = 64
+    ny: int = 64
+    D: float = 1e-3
+    dt: float = 0.1
+    theta: float = 0.5
+    linear_coef: float = 1.0
+
+    @property
+    def n_unknowns(self) -> int:
+        return self.nx * self.ny
+
+    def G(self, x):
+        u = x.reshape(self.ny, self.nx)
+        hx, hy = 1.0 / self.nx, 1.0 / self.ny
+        g = self.D * _lap5_periodic(u, hx, hy) + self.linear_coef * u - u * u * u
+        return g.reshape(-1)
+
+
+@dataclass
+class SuOlson2D(_ThetaProblem):
+    """Two-field radiation diffusion with a flux limiter and a Marshak boundary.
+
+    Unknowns (E, T) on the unit square, cell-centred, nx x ny cells.
+      radiation:  dE/dt       = div(D(E) grad E) - sigma (E - a T^4)
+      material:   d(a T^4)/dt = sigma (E - a T^4)       (c_v = 4 a T^3)
+    Face diffusion coefficient D_f = 1 / (3 sigma + R_f) with
+    R_f = sqrt(|grad E|_f^2 / Ebar_f^2 + rho^2): the normal difference across
+    the face, the tangential difference averaged over the four cells that
+    touch the face (mirror values beyond the wall), Ebar_f the mean of the two
+    cells. ``limiter=False`` gives D = 1 / (3 sigma), the linear diffusion of
+    the paper's Su-Olson system (Sec. 3.2; App. A, Su-Olson).
+    Boundaries: the left wall carries the Marshak condition
+    E/4 - (D_b/2) dE/dn = a T_b^4 / 4 with D_b = 1/(3 sigma), discretised
+    between the wall and the first cell centre, giving the inward flux
+    q = 2 D_b (4 F_inc - E_0) / (h + 4 D_b), F_inc = a T_b^4 / 4; the other
+    three walls carry zero flux.
+    """
+
+    nx: int = 64
+    ny: int = 64
+    sigma: float = 1.0
+    a: float = 1.0
+    Tb: float = 1.0
+    rho: float = 1e-6
+    limiter: bool = True
+    dt: float = 1e-3
+    theta: float = 0.5
+
+    @property
+    def n_unknowns(self) -> int:
+        return 2 * self.nx * self.ny
+
+    def _split(self, x):
+        n = self.nx * self.ny
+        return x[:n].reshape(self.ny, self.nx), x[n:].reshape(self.ny, self.nx)
+
+    def M(self, x):
+        E, T = self._split(x)
+        return np.concatenate([E.reshape(-1), (self.a * T ** 4).reshape(-1)])
+
+    def _face_coef(self, gn, gt, Ebar):
+        if not self.limiter:
+            return 1.0 / (3.0 * self.sigma) + 0.0 * gn
+        R = np.sqrt((gn * gn + gt * gt) / (Ebar * Ebar) + self.rho * self.rho)
+        return 1.0 / (3.0 * self.sigma + R)
+
+    def marshak_flux(self, E0col):
+        """Inward flux through the left wall for first-column values E0col."""
+        hx = 1.0 / self.nx
+        Db = 1.0 / (3.0 * self.sigma)
+        Finc = 0.25 * self.a * self.Tb ** 4
+        return 2.0 * Db * (4.0 * Finc - E0col) / (hx + 4.0 * Db)
+
+    def diffusion(self, E):
+        """div(D(E) grad E) with the wall conditions above; E has shape (ny, nx)."""
+        ny, nx = E.shape
+        hx, hy = 1.0 / nx, 1.0 / ny
+        jp = np.minimum(np.arange(ny) + 1, ny - 1)
+        jm = np.maximum(np.arange(ny) - 1, 0)
+        ip = np.minimum(np.arange(nx) + 1, nx - 1)
+        im = np.maximum(np.arange(nx) - 1, 0)
+        # x faces between columns i and i+1 (i = 0 .. nx-2): shape (ny, nx-1)
+        El, Er = E[:, :-1], E[:, 1:]
+        gn = (Er - El) / hx
+        Eu, Ed = E[jp, :], E[jm, :]
+        gt = ((Eu[:, :-1] + Eu[:, 1:]) - (Ed[:, :-1] + Ed[:, 1:])) / (4.0 * hy)
+        Fx_in = self._face_coef(gn, gt, 0.5 * (El + Er)) * gn     # D dE/dx at the face
+        Fx = np.zeros((ny, nx + 1), dtype=E.dtype)
+        Fx[:, 1:nx] = Fx_in
+        Fx[:, 0] = -self.marshak_flux(E[:, 0])   # D dE/dx at x = 0 is minus the inward flux
+        # y faces between rows j and j+1 (j = 0 .. ny-2): shape (ny-1, nx)
+        Eb, Et = E[:-1, :], E[1:, :]
+        gn = (Et - Eb) / hy
+        Er_, El_ = E[:, ip], E[:, im]
+        gt = ((Er_[:-1, :] + Er_[1:, :]) - (El_[:-1, :] + El_[1:, :])) / (4.0 * hx)
+        Fy_in = self._face_coef(gn, gt, 0.5 * (Eb + Et)) * gn
+        Fy = np.zeros((ny + 1, nx), dtype=E.dtype)
+        Fy[1:ny, :] = Fy_in
+        return (Fx[:, 1:] - Fx[:, :-1]) / hx + (Fy[1:, :] - Fy[:-1, :]) / hy
+
+    def G(self, x):
+        E, T = self._split(x)
+        exch = self.sigma * (E - self.a * T ** 4)
+        return np.concatenate([(self.diffusion(E) - exch).reshape(-1), exch.reshape(-1)])
+
+
+@dataclass
+class MaxwellTE2D(_ThetaProblem):
+    """Scalar TE (E_z) Helmholtz with a Kerr term, as a real map on (Re E, Im E).
+
+      G(E) = lap E + k^2 (eps_r + chi3 |E|^2) E - f
+
+    5-point Laplacian on the unit square, nx x ny cells. First-order absorbing
+    wall dE/dn = i k E (time factor e^{-i omega t}) imposed through a ghost
+    value E_g = E_0 (1 + i k h/2) / (1 - i k h/2) beyond each wall. |E|^2 =
+    Re^2 + Im^2 is not holomorphic in E, so the unknowns are the two real
+    planes and the Jacobian is the real 2N x 2N one. This is the scalar
+    variant of the paper's Kerr problem (Sec. 3.2; App. A, Time-Harmonic
+    Maxwell's Equations in Kerr Media); a boundary-value problem, F = G.
+    """
+
+    nx: int = 64
+    ny: int = 64
+    k: float = 10.0
+    chi3: float = 1e-3
+    eps_r: np.ndarray = field(default=None, repr=False)
+    f: np.ndarray = field(default=None, repr=False)
+    bvp = True
+
+    @property
+    def n_unknowns(self) -> int:
+        return 2 * self.nx * self.ny
+
+    def ghost_coef(self, h):
+        z = (1.0 + 0.5j * self.k * h) / (1.0 - 0.5j * self.k * h)
+        return z.real, z.imag
+
+    def G(self, x):
+        ny, nx = self.ny, self.nx
+        n = nx * ny
+        A = x[:n].reshape(ny, nx)
+        B = x[n:].reshape(ny, nx)
+        hx, hy = 1.0 / nx, 1.0 / ny
+        cxr, cxi = self.ghost_coef(hx)
+        cyr, cyi = self.ghost_coef(hy)
+
+        def lap(P, Q, sgn):
+            # P is the plane itself, Q the other plane. The ghost beyond each
+            # wall is c E_wall: Re = cr a - ci b, Im = cr b + ci a, i.e.
+            # cr * P_wall + sgn * ci * Q_wall with sgn = -1 for Re, +1 for Im.
+            west = np.concatenate([(cxr * P[:, :1] + sgn * cxi * Q[:, :1]), P[:, :-1]], axis=1)
+            east = np.concatenate([P[:, 1:], (cxr * P[:, -1:] + sgn * cxi * Q[:, -1:])], axis=1)
+            south = np.concatenate([(cyr * P[:1, :] + sgn * cyi * Q[:1, :]), P[:-1, :]], axis=0)
+            north = np.concatenate([P[1:, :], (cyr * P[-1:, :] + sgn * cyi * Q[-1:, :])], axis=0)
+            return (east - 2.0 * P + west) / (hx * hx) + (north - 2.0 * P + south) / (hy * hy)
+
+        eps = self.eps_r.reshape(ny, nx) if self.eps_r is not None else np.ones((ny, nx))
+        src = self.f if self.f is not None else np.zeros(2 * n)
+        coef = self.k * self.k * (eps + self.chi3 * (A * A + B * B))
+        Gr = lap(A, B, -1.0) + coef * A - src[:n].reshape(ny, nx)
+        Gi = lap(B, A, +1.0) + coef * B - src[n:].reshape(ny, nx)
+        return np.concatenate([Gr.reshape(-1), Gi.reshape(-1)])
+
+
+def make(pde: str, **kw):
+    """Construct a problem by name: burgers1d, allen_cahn, su_olson, maxwell."""
+    return {"burgers1d": Burgers1D, "allen_cahn": AllenCahn2D,
+            "su_olson": SuOlson2D, "maxwell": MaxwellTE2D}[pde](**kw)

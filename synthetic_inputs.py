@@ -1,0 +1,115 @@
+"""Seeded synthetic inputs shared by the oracle, the tests and the benchmark.
+
+This module holds only input generation: initial states, media and sources
+drawn from fixed seeds. It contains none of the solver's arithmetic (no
+residual, no derivative, no Krylov or Newton step), so that the CPU oracle
+and the CUDA path can both consume the same inputs without sharing any code
+of the method itself.
+
+Layout of every state vector: one contiguous float64 array, field-major,
+then row-major (y, x): index = f * ny * nx + j * nx + i. Cell centres of the
+2D grids are at ((i + 1/2) / nx, (j + 1/2) / ny) on the unit square; the 1D
+Burgers line has cells at x_i = i / N.
+"""
+from __future__ import annotations
+
+import math
+
+import numpy as np
+
+
+def burgers_ic(N: int = 1024, seed: int = 0) -> np.ndarray:
+    """Noisy sine wave for the 1D viscous Burgers step.
+
+    u0_i = sin(2 pi x_i) + 0.1 * eta_i with x_i = i / N, where eta is standard
+    normal noise from ``default_rng(seed)`` smoothed by three periodic passes
+    of the (1, 2, 1) / 4 filter (damped Jacobi on the noise only).
+    """
+    rng = np.random.default_rng(seed)
+    eta = rng.standard_normal(N)
+    for _ in range(3):
+        eta = 0.25 * (np.roll(eta, 1) + 2.0 * eta + np.roll(eta, -1))
+    x = np.arange(N, dtype=np.float64) / N
+    return np.sin(2.0 * math.pi * x) + 0.1 * eta
+
+
+def allen_cahn_ic(nx: int, ny: int | None = None, seed: int = 0) -> np.ndarray:
+    """Uniform noise in [-0.1, 0.1] on an nx x ny periodic grid (flat, row-major)."""
+    ny = nx if ny is None else ny
+    rng = np.random.default_rng(seed)
+    return rng.uniform(-0.1, 0.1, size=ny * nx).astype(np.float64)
+
+
+def su_olson_ic(nx: int, ny: int | None = None, E0: float = 1e-6, a: float = 1.0) -> np.ndarray:
+    """Cold start in equilibrium: E = E0 and a T^4 = E0 everywhere; returns [E, T] flat."""
+    ny = nx if ny is None else ny
+    n = nx * ny
+    T0 = (E0 / a) ** 0.25
+    return np.concatenate([np.full(n, E0), np.full(n, T0)])
+
+
+def maxwell_medium(nx: int, ny: int | None = None, seed: int = 0, n_disc: int = 16,
+                   r_lo: float = 0.02, r_hi: float = 0.08,
+                   eps_lo: float = 1.0, eps_hi: float = 4.0) -> np.ndarray:
+    """Piecewise-constant relative permittivity: background 1 plus random discs.
+
+    Disc d has centre U[0,1]^2, radius U[r_lo, r_hi] and permittivity
+    U[eps_lo, eps_hi], all drawn from ``default_rng(seed)`` in that order per
+    disc; later discs overwrite earlier ones. Returns a flat (ny * nx) array.
+    """
+    ny = nx if ny is None else ny
+    rng = np.random.default_rng(seed)
+    xc = (np.arange(nx) + 0.5) / nx
+    yc = (np.arange(ny) + 0.5) / ny
+    X, Y = np.meshgrid(xc, yc)
+    eps = np.ones((ny, nx))
+    for _ in range(n_disc):
+        cx, cy = rng.uniform(0.0, 1.0, size=2)
+        r = rng.uniform(r_lo, r_hi)
+        e = rng.uniform(eps_lo, eps_hi)
+        eps[(X - cx) ** 2 + (Y - cy) ** 2 <= r * r] = e
+    return eps.reshape(-1)
+
+
+def maxwell_point_source(nx: int, ny: int | None = None) -> np.ndarray:
+    """Point source of unit total strength at cell (nx // 2, ny // 2).
+
+    Returns [f_re, f_im] flat (2 * ny * nx); f_re = 1 / (hx * hy) at that cell.
+    """
+    ny = nx if ny is None else ny
+    f = np.zeros(2 * nx * ny)
+    f[(ny // 2) * nx + nx // 2] = float(nx * ny)
+    return f
+
+
+def maxwell_wavenumber(n: int, ppw: float = 10.0, eps_max: float = 4.0) -> float:
+    """Wavenumber giving ``ppw`` cells per wavelength in the densest medium.
+
+    k * sqrt(eps_max) * h = 2 pi / ppw with h = 1 / n.
+    """
+    return 2.0 * math.pi * n / (ppw * math.sqrt(eps_max))
+
+
+def serving_requests(n_req: int, rate: float, seed: int = 0,
+                     n_lo: int = 64, n_hi: int = 2048, tile: int = 64,
+                     steps_hi: int = 20) -> list[dict]:
+    """Poisson stream of mixed solves (arrival time, PDE, grid, steps, precision).
+
+    Inter-arrival gaps are exponential with mean 1 / rate seconds. The PDE is
+    uniform over the three 2D problems, the side n is log-uniform in
+    [n_lo, n_hi] rounded down to a multiple of ``tile``, the step count is
+    uniform in 1..steps_hi and the precision is uniform over {"mixed", "fp64"}.
+    """
+    rng = np.random.default_rng(seed)
+    t = 0.0
+    out = []
+    for r in range(n_req):
+        t += rng.exponential(1.0 / rate)
+        pde = ["allen_cahn", "su_olson", "maxwell"][int(rng.integers(0, 3))]
+        n = int(math.exp(rng.uniform(math.log(n_lo), math.log(n_hi))))
+        n = max(tile, (n // tile) * tile)
+        steps = int(rng.integers(1, steps_hi + 1))
+        prec = ["mixed", "fp64"][int(rng.integers(0, 2))]
+        out.append({"id": r, "t_arrival": t, "pde": pde, "n": n, "steps": steps,
+                    "precision": prec, "seed": int(rng.integers(0, 2**31 - 1))})
+    return out

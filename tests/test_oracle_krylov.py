@@ -1,0 +1,109 @@
+"""Pins of the oracle's Krylov solvers against library routines (CPU only).
+
+* GMRES without restart on an N <= 32 system reaches numpy.linalg.solve.
+* After k Arnoldi steps GMRES returns the minimum-residual point of the
+  Krylov space K_k of Eq. 10 (computed here by numpy.linalg.lstsq on an
+  explicit power basis), which pins the Givens least squares.
+* Restarted GMRES, BiCGSTAB and CG meet their relative tolerance on the true
+  residual; CG on an SPD system and BiCGSTAB agree with numpy's solve.
+* A circulant Allen-Cahn Jacobian (linearised at a constant state) is
+  inverted exactly by FFT; GMRES with the complex-step JVP matches it.
+* A forced BiCGSTAB breakdown (r_hat . A r0 = 0) is reported, not hidden.
+"""
+import numpy as np
+import pytest
+
+from oracle import jvp, krylov, pdes
+
+
+def _nonsym(rng, n, shift=4.0):
+    return rng.standard_normal((n, n)) / np.sqrt(n) + shift * np.eye(n)
+
+
+def test_gmres_full_equals_dense_solve(rng):
+    n = 32
+    A = _nonsym(rng, n, 1.0)
+    b = rng.standard_normal(n)
+    r = krylov.gmres(lambda v: A @ v, b, m=n, tol=1e-14, max_cycles=1)
+    assert r.converged
+    assert np.allclose(r.x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_gmres_is_minimum_residual_over_krylov_space(rng, k):
+    n = 24
+    A = _nonsym(rng, n, 0.5)
+    b = rng.standard_normal(n)
+    r = krylov.gmres(lambda v: A @ v, b, m=k, tol=0.0, max_cycles=1)
+    assert r.iterations == k
+    # explicit basis of K_k = span{b, Ab, ..., A^{k-1} b}, orthonormalised by QR
+    K = np.empty((n, k))
+    K[:, 0] = b
+    for i in range(1, k):
+        K[:, i] = A @ K[:, i - 1]
+    Q, _ = np.linalg.qr(K)
+    c = np.linalg.lstsq(A @ Q, b, rcond=None)[0]
+    x_min = Q @ c
+    assert np.allclose(r.x, x_min, rtol=1e-8, atol=1e-10)
+    assert abs(r.resid_est - np.linalg.norm(b - A @ r.x)) <= 1e-9 * np.linalg.norm(b)
+
+
+def test_givens_rotation():
+    for f, g in [(3.0, 4.0), (-2.0, 0.5), (0.0, -1.0), (-1.0, 0.0), (0.0, 0.0)]:
+        c, s = krylov.givens(f, g)
+        assert c * c + s * s == pytest.approx(1.0)
+        assert -s * f + c * g == pytest.approx(0.0, abs=1e-15)
+        assert c * f + s * g == pytest.approx(np.hypot(f, g))
+
+
+def test_restarted_gmres_meets_tolerance(rng):
+    n = 200
+    A = _nonsym(rng, n, 2.0)
+    b = rng.standard_normal(n)
+    r = krylov.gmres(lambda v: A @ v, b, m=10, tol=1e-10, max_cycles=200)
+    assert r.converged
+    assert np.linalg.norm(b - A @ r.x) <= 1.01e-10 * np.linalg.norm(b)
+    assert r.matvecs == r.iterations + (r.iterations - 1) // 10   # one true-residual product per restart
+
+
+def test_bicgstab_and_cg_against_solve(rng):
+    n = 60
+    A = _nonsym(rng, n, 3.0)
+    b = rng.standard_normal(n)
+    r = krylov.bicgstab(lambda v: A @ v, b, tol=1e-12, maxiter=500)
+    assert r.converged and not r.breakdown
+    assert np.allclose(r.x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-10)
+    B = rng.standard_normal((n, n))
+    S = B @ B.T / n + np.eye(n)
+    r = krylov.cg(lambda v: S @ v, b, tol=1e-12, maxiter=500)
+    assert r.converged
+    assert np.allclose(r.x, np.linalg.solve(S, b), rtol=1e-9, atol=1e-10)
+
+
+def test_bicgstab_breakdown_is_reported():
+    A = np.array([[0.0, -1.0], [1.0, 0.0]])   # rotation by 90 degrees: b . A b = 0
+    r = krylov.bicgstab(lambda v: A @ v, np.array([1.0, 0.0]), tol=1e-12, maxiter=10)
+    assert r.breakdown and not r.converged
+
+
+def test_zero_rhs_returns_zero():
+    for solve in (lambda A, b: krylov.gmres(A, b, 5, 1e-8, 3), lambda A, b: krylov.bicgstab(A, b, 1e-8, 3),
+                  lambda A, b: krylov.cg(A, b, 1e-8, 3)):
+        r = solve(lambda v: 2.0 * v, np.zeros(7))
+        assert r.converged and r.iterations == 0 and not r.x.any()
+
+
+def test_gmres_on_circulant_allen_cahn_matches_fft():
+    """Linearised at u = c the Allen-Cahn Jacobian is circulant: J^{-1} b by FFT is exact."""
+    n, D, dt, th, c = 32, 1e-3, 0.1, 0.5, 0.4
+    p = pdes.AllenCahn2D(nx=n, ny=n, D=D, dt=dt, theta=th)
+    u = np.full(n * n, c)
+    b = np.random.default_rng(7).standard_normal(n * n)
+    F = lambda z: p.residual(z, p.rhs(u))
+    r = krylov.gmres(lambda v: jvp.jvp_complex_step(F, u, v)[1], b, m=40, tol=1e-12, max_cycles=50)
+    assert r.converged
+    k = np.fft.fftfreq(n, d=1.0 / n)
+    sym1 = (2 * np.cos(2 * np.pi * k / n) - 2) * n * n              # eigenvalues of the periodic 1D second difference
+    lam = 1.0 - th * dt * (D * (sym1[None, :] + sym1[:, None]) + 1.0 - 3.0 * c * c)
+    x_fft = np.real(np.fft.ifft2(np.fft.fft2(b.reshape(n, n)) / lam)).reshape(-1)
+    assert np.allclose(r.x, x_fft, rtol=1e-9, atol=1e-10 * np.abs(x_fft).max())
