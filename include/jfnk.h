@@ -1,0 +1,187 @@
+/*
+ * jfnk.h -- C ABI of libjfnk, a GB300 (sm_103a) implementation of the
+ * matrix-free Jacobian-free Newton-Krylov (JFNK) hot path of
+ * "Robust Matrix-Free Newton-Krylov Solvers via Automatic Differentiation".
+ *
+ * The method solves the discrete residual equation F(x^k, x*) = 0 (Eq. 2) by
+ * Newton's method, J(x^k) dx = -F(x^k) (Eq. 4), with the relative stopping
+ * test ||F(x^k)|| / ||F(x*)|| < tol_Newton (Eq. 5) and a backtracking line
+ * search (Sec. 2). The Newton system is solved by a Krylov method that sees
+ * the Jacobian only through Jacobian-vector products (Sec. 3.1): either the
+ * forward-mode AD product jvp(F, x, v) = (F(x), J(x) v) (Eq. 9), computed
+ * here by one dual-number sweep of the residual stencil, or the finite-
+ * difference quotient (F(x + eps v) - F(x)) / eps (Eq. 7) with the step of
+ * Eq. 8 or the scaled rule sqrt(eps_mach) (1 + ||x||) / ||v||.
+ *
+ * Conventions for every entry point:
+ *  - Status: every function returns a jfnk_status; nothing aborts, exits or
+ *    throws across the ABI. jfnk_last_error() gives the message of the last
+ *    failure on a context.
+ *  - Arrays: contiguous structure-of-arrays planes, field-major, then
+ *    row-major (y, x): element (f, j, i) is at f * ny * nx + j * nx + i. The
+ *    1D Burgers problem has ny = 1.
+ *  - Ownership: array arguments are borrowed. Device pointers must stay
+ *    valid until the call returns (every call below is synchronous with
+ *    respect to the context's stream unless stated). Host pointers are
+ *    accepted where stated; the library then copies through its own device
+ *    buffers. The context owns all workspace and frees it in jfnk_destroy.
+ *  - Threads: a context is used by one host thread at a time.
+ */
+#ifndef JFNK_H
+#define JFNK_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define JFNK_ABI_VERSION 1
+#define JFNK_MAX_RESTART 64   /* largest GMRES restart length m */
+
+typedef struct jfnk_ctx jfnk_ctx;
+
+typedef enum {
+  JFNK_OK = 0,
+  JFNK_E_INVALID = 1,        /* bad argument; nothing was done */
+  JFNK_E_OOM = 2,            /* workspace would exceed the HBM budget or cudaMalloc failed */
+  JFNK_E_CUDA = 3,           /* a CUDA runtime call failed; see jfnk_last_error */
+  JFNK_E_NOT_CONVERGED = 4,  /* Newton reached max_newton without meeting tol_Newton */
+  JFNK_E_BREAKDOWN = 5,      /* Krylov breakdown (BiCGSTAB rho, r_hat.v or omega = 0; CG p.Ap = 0) */
+  JFNK_E_NONFINITE = 6,      /* a residual norm or Krylov scalar became Inf/NaN */
+  JFNK_E_LINESEARCH = 7,     /* reserved: line search failures are counted, not fatal */
+  JFNK_E_TIMEOUT = 8,        /* a bounded device wait expired */
+  JFNK_E_BUSY = 9            /* jfnk_poll: the request is still running */
+} jfnk_status;
+
+typedef enum { JFNK_AD = 0, JFNK_FD = 1 } jfnk_linearisation;
+typedef enum { JFNK_GMRES = 0, JFNK_BICGSTAB = 1, JFNK_CG = 2 } jfnk_krylov;
+typedef enum {
+  JFNK_BURGERS1D = 0,     /* p[0] = nu                                              */
+  JFNK_ALLEN_CAHN2D = 1,  /* p[0] = D, p[1] = coefficient of the +u term (1 or 0)   */
+  JFNK_SU_OLSON2D = 2,    /* p[0] = sigma, p[1] = a, p[2] = T_b, p[3] = rho,
+                             p[4] = 1 flux limiter on / 0 off                        */
+  JFNK_MAXWELL_TE2D = 3   /* p[0] = k, p[1] = chi3; aux[0] = eps_r (nx*ny),
+                             aux[1] = source (Re plane, Im plane; 2*nx*ny)           */
+} jfnk_pde;
+typedef enum {
+  JFNK_FP64 = 0,        /* everything in FP64                                                 */
+  JFNK_FP32 = 1,        /* state, residual, JVP and basis in FP32 (Hessenberg in FP64)        */
+  JFNK_MIXED_FP32 = 2,  /* FP64 state, residual, update, line search and Hessenberg;
+                           JVP and Krylov vectors in FP32                                     */
+  JFNK_MIXED_BF16 = 3   /* as MIXED_FP32 with the GMRES basis stored in BF16                  */
+} jfnk_precision;
+typedef enum { JFNK_EPS_SCALED = 0, JFNK_EPS_PAPER = 1 } jfnk_fd_rule;
+
+/* One nonlinear problem: PDE, grid and time step (App. A and the benchmark
+ * variants). The implicit step is the theta-method residual
+ *   F(x; b) = M(x) - theta dt G(x) - b,   b = M(x^n) + (1 - theta) dt G(x^n),
+ * M the identity except for the radiation problem (material energy a T^4).
+ * theta = 1/2 is the paper's Crank-Nicolson; 1 is backward Euler. The
+ * Maxwell problem is a boundary-value problem, F = G (dt, theta unused). */
+typedef struct {
+  int pde;            /* jfnk_pde */
+  int nx, ny;         /* cells; ny = 1 for Burgers */
+  double dt, theta;
+  double p[8];        /* PDE parameters, see jfnk_pde */
+  const double* aux[2];  /* Maxwell eps_r and source, FP64, host or device;
+                            copied by jfnk_set_problem; NULL: eps_r = 1, no source */
+} jfnk_problem;
+
+typedef struct {
+  int lin;            /* jfnk_linearisation */
+  int krylov;         /* jfnk_krylov */
+  int prec;           /* jfnk_precision */
+  int restart;        /* GMRES restart length m, 1..JFNK_MAX_RESTART */
+  int max_newton;     /* Newton iterations per nonlinear solve */
+  int max_krylov;     /* GMRES restart cycles; BiCGSTAB / CG iterations */
+  double tol_newton;  /* Eq. 5 */
+  double tol_krylov;  /* ||r|| <= tol_krylov ||b|| */
+  int fd_rule;        /* jfnk_fd_rule */
+  double fd_eps;      /* > 0: fixed FD step instead of the rule */
+  double ls_c1;       /* Armijo constant: accept ||F(x+a dx)|| <= (1 - c1 a) ||F(x)|| */
+  double ls_min_alpha;/* smallest trial step; accepted when no trial passes */
+  int born_start;     /* Maxwell: solve the chi3 = 0 problem from zero first */
+} jfnk_opts;
+
+typedef struct {
+  int status;           /* jfnk_status of the last nonlinear solve */
+  int steps_done;       /* implicit steps completed */
+  int steps_failed;     /* steps whose final ||F||/||F0|| missed 100 x tol_newton */
+  int newton_its, krylov_its, jvp_calls, ls_backtracks, ls_failures, krylov_failures;
+  double res0;          /* ||F(x*)|| of the last solve (Eq. 5 denominator) */
+  double res_final;     /* final ||F|| of the last solve */
+  double ms;            /* host wall time of the call */
+} jfnk_report;
+
+/* Defaults of the paper for a precision (Sec. 3.3): tol_Newton 1e-6 / 1e-4,
+ * tol_Krylov 1e-8 / 1e-6 (FP64 / FP32), 15 Newton iterations, 100 Krylov
+ * cycles, GMRES(30), AD, scaled FD rule, c1 = 1e-4, alpha_min = 2^-10. */
+void jfnk_default_opts(jfnk_opts* opts, int prec);
+
+/* Create a context on CUDA device `device`. hbm_budget caps the workspace
+ * the context may allocate (0: no cap). cuda_stream is a cudaStream_t to
+ * issue all work on (NULL: the context creates its own non-blocking stream).
+ * Returns JFNK_E_INVALID for a bad device, JFNK_E_CUDA on runtime errors. */
+jfnk_status jfnk_create(jfnk_ctx** out, int device, size_t hbm_budget, void* cuda_stream);
+
+/* Validate and install a problem; copies aux arrays. Workspace for the
+ * Krylov solver is sized lazily by jfnk_solve. JFNK_E_INVALID on bad sizes
+ * or parameters. */
+jfnk_status jfnk_set_problem(jfnk_ctx* ctx, const jfnk_problem* prob);
+
+/* One Jacobian-vector product of the installed residual at x along v.
+ * lin = JFNK_AD: one dual-number sweep gives F(x) (written to F_out when it
+ * is not NULL) and J(x) v (Eq. 9). lin = JFNK_FD: (F(x + eps v) - F(x))/eps
+ * (Eq. 7) with eps = fd_eps when fd_eps > 0, else the scaled rule
+ * sqrt(eps_mach)(1 + ||x||)/||v|| (both norms reduced on the device; v = 0
+ * is JFNK_E_INVALID through a non-finite step). prec = JFNK_FP64: x, v, b,
+ * F_out, Jv_out are double; JFNK_FP32: float. b is the constant part of the
+ * theta-method residual (NULL: zero). All pointers are device pointers; the
+ * call is stream-ordered and returns after the work is queued. */
+jfnk_status jfnk_jvp(jfnk_ctx* ctx, int lin, int prec, const void* x, const void* v,
+                     const void* b, void* F_out, void* Jv_out, double fd_eps);
+
+/* Residual of the installed problem: F_out = F(x; b) in precision prec
+ * (device pointers, stream-ordered). */
+jfnk_status jfnk_residual(jfnk_ctx* ctx, int prec, const void* x, const void* b, void* F_out);
+
+/* Solve `steps` implicit steps from x_prev (NULL: from x_inout), writing the
+ * final state to x_inout; for the Maxwell problem one nonlinear solve from
+ * x_inout (or the Born start). x_prev and x_inout are FP64, host or device.
+ * Synchronous. Returns JFNK_OK when every step converged, otherwise the
+ * status of the first failing step; rep (host, may be NULL) gets counts. */
+jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_prev,
+                       double* x_inout, int steps, jfnk_report* rep);
+
+/* Serving: queue a solve of `prob` (steps as in jfnk_solve) and return a
+ * ticket at once. x0 and x_out are FP64 host or device arrays that must stay
+ * valid until jfnk_poll returns a final status for the ticket. Requests are
+ * admitted when their workspace fits the context's HBM budget and a slot is
+ * free; admitted requests run concurrently on the device. */
+jfnk_status jfnk_submit(jfnk_ctx* ctx, const jfnk_problem* prob, const jfnk_opts* opts,
+                        const double* x0, double* x_out, int steps, unsigned long long* ticket);
+
+/* JFNK_E_BUSY while the request runs; otherwise its final status, with rep
+ * (may be NULL) filled in. Unknown tickets give JFNK_E_INVALID. */
+jfnk_status jfnk_poll(jfnk_ctx* ctx, unsigned long long ticket, jfnk_report* rep);
+
+/* Per-kernel timing: when enabled, each kernel class launched by the
+ * context is bracketed by CUDA events on the context's stream and its
+ * device time accumulated. jfnk_kernel_stats fills, for kernel class i,
+ * names[i] (static strings), launches[i], total_ms[i] and bytes[i] (the
+ * algorithmic bytes those launches had to move) for up to cap classes and
+ * returns the number of classes. Reset clears the counters. */
+jfnk_status jfnk_set_timing(jfnk_ctx* ctx, int enable);
+int jfnk_kernel_stats(jfnk_ctx* ctx, const char** names, long long* launches,
+                      double* total_ms, double* bytes, int cap);
+void jfnk_reset_stats(jfnk_ctx* ctx);
+
+const char* jfnk_last_error(const jfnk_ctx* ctx);
+const char* jfnk_status_string(int status);
+void jfnk_destroy(jfnk_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* JFNK_H */

@@ -1,0 +1,72 @@
+// kernels.h -- host-side launch interface between the library's translation
+// units (stencil kernels, Krylov kernels, the C ABI driver). Internal; not
+// part of the C ABI.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stddef.h>
+
+#include "pdes.cuh"
+
+namespace jfnk {
+
+enum VType { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2 };
+inline size_t vt_size(int t) { return t == VT_F64 ? 8 : (t == VT_F32 ? 4 : 2); }
+
+// Device workspace of one reduction site (partials + arrival counter).
+struct RedWs {
+  void* partials;          // kMaxVecBlocks-or-more blocks x kMaxK accumulators (8 bytes each)
+  unsigned int* counter;   // zero between launches
+  int max_blocks;          // capacity of partials in blocks
+};
+
+// Scalar post-processing done by the last block of a reduction (thread 0).
+enum PostOp {
+  POST_NONE = 0,
+  POST_GMRES_RESTART = 1,   // sums[0] = ||r||^2: set beta, scale[0], g[0], convergence
+  POST_NORM_EPS = 2,        // sums -> FD step into post_arg (see krylov.cu)
+};
+
+// Stencil geometry shared by all stencil kernels of a problem.
+struct StencilGeom {
+  dim3 block, grid;
+  int rows_per_thread;     // R: each thread handles R rows strided by blockDim.y
+  int nblocks;             // grid.x * grid.y
+};
+StencilGeom stencil_geom(const ProbDev& P);
+
+// F = F(x + alpha d; b) in precision t (x, d, b, F, xout of type t; d, b,
+// F, xout, x32 may be null). sums[0] = ||F||^2, sums[1] = ||x + alpha d||^2
+// (double) when sums != null.
+cudaError_t launch_residual(const ProbDev& P, int t, const void* x, const void* d, double alpha,
+                            const void* b, void* F, void* xout, float* x32, RedWs red, double* sums,
+                            cudaStream_t st);
+
+// b = M(xn) + (1 - theta) dt G(xn) in precision t.
+cudaError_t launch_rhs(const ProbDev& P, int t, const void* xn, void* b, cudaStream_t st);
+
+// Jacobian-vector product in precision t (x, b, F, out, add, dw of type t;
+// v of type tv = t or BF16 when t = FP32).
+//   AD: (F, Jv) by one dual-number sweep; FD: Jv = (F(x + eps s v) - Fx)/eps.
+//   The direction is s v with s = *vscale (null: 1).
+//   out = c_jv * Jv + c_add * add (add may be null); F (AD only) may be null.
+//   ndots in 0..3 reductions of out . dw[k] (dw[k] null: out . out) into
+//   sums[k] (double), then the post-operation `post` on the last block.
+// FD step: eps_fixed > 0 uses it; else rule 0 (scaled):
+//   eps = sqrt(eps_mach)(1 + sqrt(*xn2)) / (sqrt(*vn2) s), vn2 null meaning
+//   ||v|| = 1 after scaling; rule 1 (paper): sqrt(eps_mach) max(1, sqrt(*xn2)).
+struct JvpArgs {
+  int lin;                     // 0 AD, 1 FD
+  int t, tv;
+  const void* x; const void* v; const double* vscale;
+  const void* b; void* F; const void* Fx;
+  void* out; double c_jv; const void* add; double c_add;
+  int ndots; const void* dw[3]; double* sums;
+  int post; void* post_arg;
+  double eps_fixed; int eps_rule; const double* xn2; const double* vn2;
+  float* eps_out;              // FD: the step used (for reporting), may be null
+  const int* active;           // device flag: the kernel does nothing when *active == 0 (null: always run)
+};
+cudaError_t launch_jvp(const ProbDev& P, const JvpArgs& a, RedWs red, cudaStream_t st);
+
+}  // namespace jfnk

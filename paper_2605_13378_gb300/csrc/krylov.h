@@ -1,0 +1,34 @@
+// krylov.h -- host launch interface of the flat-vector Krylov kernels.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include "kernels.h"
+#include "ctl.cuh"
+
+namespace jfnk {
+
+// Vectors of one BiCGSTAB solve (JVP precision except F (state) and d).
+struct BicgVecs {
+  const void* F; void* r; void* rhat; void* p; void* v; void* s; void* t; void* d;
+  const double* sums;   // init: sums[0] = ||F||^2
+  double* pn2; double* sn2;
+};
+
+// One CGS2 pass (1: dots, 2: update + dots, 3: update + norm + Givens) of
+// Arnoldi step k - 1 over basis vectors 0 .. k-1.
+cudaError_t launch_arnoldi_pass(int pass, int tb, int tj, long long n, void* V, int k, void* w, GmresCtl* ctl,
+                                RedWs red, cudaStream_t st);
+cudaError_t launch_gmres_init(int ts, int tj, int tb, int td, long long n, const void* F, void* u0, void* rhs,
+                              void* d, GmresCtl* ctl, const double* sums, double tol, int m, cudaStream_t st);
+// back substitution + d += V y over at most kmax vectors
+cudaError_t launch_gmres_finish(int tb, int td, long long n, const void* V, void* d, GmresCtl* ctl, int kmax,
+                                cudaStream_t st);
+cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);
+cudaError_t launch_vdots(int t, long long n, int nd, const void* const* a, const void* const* b, double* sums,
+                         RedWs red, const int* active, cudaStream_t st);
+// phase 0 init, 1 p-update, 2 s-update, 3 half-step x update, 4 x/r update
+cudaError_t launch_bicg(int phase, int ts, int tj, int td, long long n, const BicgVecs& vv, BicgCtl* c,
+                        RedWs red, int it, double tol, cudaStream_t st);
+
+}  // namespace jfnk

@@ -1,0 +1,209 @@
+"""Parity of full Newton-Krylov solves on the GPU with the CPU oracle (GPU).
+
+Each case solves the same seeded problem through jfnk_solve and through
+oracle.newton, then compares:
+* the solution, relative to max |x|: 1e-10 in FP64 and 1e-5 for the FP32 and
+  mixed-precision forms (the stated solution tolerances of the method);
+* the final nonlinear residual, recomputed by the oracle on the GPU's
+  solution: below tol_Newton relative to ||F(x*)|| (Eq. 5);
+* Newton iteration counts: equal (FP64); Krylov counts within 2 per Newton
+  step (the reduction order differs, so a convergence test can flip by one
+  iteration near its threshold).
+Also: the 1D Burgers step at the benchmark size (N = 1024), time stepping
+over several steps, BiCGSTAB, FD, the Born start of the Maxwell problem, an
+already-converged start, determinism, and the largest restart length.
+"""
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import newton as onw, pdes as opdes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def J():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13378_gb300 import build
+    build.build()
+    from paper_2605_13378_gb300 import jfnk
+    return jfnk
+
+
+@pytest.fixture
+def ctx(J):
+    c = J.jfnk_create(0)
+    yield c
+    J.jfnk_destroy(c)
+
+
+def _opts(J, prec, lin="ad", krylov="gmres", restart=30, tol_n=1e-10, tol_k=1e-10, max_newton=15, max_krylov=100):
+    o = J.jfnk_default_opts(prec)
+    o.lin = J.JFNK_AD if lin == "ad" else J.JFNK_FD
+    o.krylov = J.JFNK_GMRES if krylov == "gmres" else J.JFNK_BICGSTAB
+    o.restart, o.tol_newton, o.tol_krylov = restart, tol_n, tol_k
+    o.max_newton, o.max_krylov = max_newton, max_krylov
+    return o
+
+
+def _oopts(lin="ad", krylov="gmres", restart=30, tol_n=1e-10, tol_k=1e-10, max_newton=15, max_krylov=100):
+    return onw.Options(lin=lin, krylov=krylov, restart=restart, tol_newton=tol_n, tol_krylov=tol_k,
+                       max_newton=max_newton, max_cycles=max_krylov)
+
+
+def _run(J, ctx, lp, opts, x0, steps):
+    J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+    x = torch.tensor(x0, device="cuda")
+    rep = J.jfnk_report()
+    s = J.jfnk_solve(ctx, opts, None, x, steps, rep)
+    torch.cuda.synchronize()
+    return s, x.cpu().numpy(), rep
+
+
+def _compare(x, x_ref, rep, reps, tol_x, exact_newton=True):
+    err = np.abs(x - x_ref).max() / np.abs(x_ref).max()
+    assert err <= tol_x, err
+    nn = sum(r.newton_its for r in reps)
+    if exact_newton:
+        assert rep.newton_its == nn, (rep.newton_its, nn)
+    kk = sum(r.krylov_its for r in reps)
+    assert abs(rep.krylov_its - kk) <= 2 * max(nn, 1), (rep.krylov_its, kk)
+
+
+@pytest.mark.parametrize("lin", ["ad", "fd"])
+def test_burgers_1024_one_step_fp64(J, ctx, lin):
+    N = 1024
+    u0 = si.burgers_ic(N, 0)
+    p = opdes.Burgers1D(N=N, nu=1e-2, dt=1e-3)
+    lp = J.make_problem("burgers1d", N, 1, 1e-3, 1.0, (1e-2,))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, lin), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts(lin))
+    _compare(x, x_ref, rep, reps, 1e-10)
+    assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-10 * reps[0].res0
+    # mass is conserved by the periodic flux form
+    assert abs(x.sum() - u0.sum()) <= 1e-8 * np.abs(u0).sum()
+
+
+@pytest.mark.parametrize("krylov", ["gmres", "bicgstab"])
+@pytest.mark.parametrize("lin", ["ad", "fd"])
+def test_allen_cahn_two_steps_fp64(J, ctx, lin, krylov):
+    n = 72
+    u0 = si.allen_cahn_ic(n, n, 3)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, lin, krylov, 40), u0, 2)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 2, _oopts(lin, krylov, 40))
+    _compare(x, x_ref, rep, reps, 1e-10)
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16", "fp32"])
+def test_allen_cahn_reduced_precision(J, ctx, prec):
+    n = 72
+    u0 = si.allen_cahn_ic(n, n, 5)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    code = {"mixed": J.JFNK_MIXED_FP32, "bf16": J.JFNK_MIXED_BF16, "fp32": J.JFNK_FP32}[prec]
+    tol_n = 1e-4 if prec == "fp32" else 1e-9
+    tol_k = 1e-5 if prec != "bf16" else 1e-2
+    s, x, rep = _run(J, ctx, lp, _opts(J, code, "ad", "gmres", 40, tol_n, tol_k, max_newton=30), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts("ad", "gmres", 40, 1e-12, 1e-12))
+    err = np.abs(x - x_ref).max() / np.abs(x_ref).max()
+    assert err <= 1e-5, err
+    if prec != "fp32":   # FP64 outer residual: the nonlinear residual meets its FP64 tolerance
+        assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= tol_n * reps[0].res0 * 1.0001
+
+
+@pytest.mark.parametrize("limiter", [1.0, 0.0])
+def test_su_olson_step_fp64(J, ctx, limiter):
+    n = 40
+    x0 = si.su_olson_ic(n, n)
+    p = opdes.SuOlson2D(nx=n, ny=n, dt=1e-3, theta=0.5, limiter=bool(limiter))
+    lp = J.make_problem("su_olson", n, n, 1e-3, 0.5, (1.0, 1.0, 1.0, 1e-6, limiter))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, "ad", "gmres", 30, 1e-9, 1e-10), x0, 2)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, x0, 2, _oopts("ad", "gmres", 30, 1e-9, 1e-10))
+    _compare(x, x_ref, rep, reps, 1e-10)
+
+
+def test_su_olson_mixed(J, ctx):
+    n = 40
+    x0 = si.su_olson_ic(n, n)
+    p = opdes.SuOlson2D(nx=n, ny=n, dt=1e-3, theta=0.5)
+    lp = J.make_problem("su_olson", n, n, 1e-3, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_MIXED_FP32, "ad", "gmres", 30, 1e-8, 1e-5, 30), x0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, x0, 1, _oopts("ad", "gmres", 30, 1e-12, 1e-12))
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5
+
+
+@pytest.mark.parametrize("lin", ["ad", "fd"])
+def test_maxwell_born_start_and_newton_fp64(J, ctx, lin):
+    n, k, chi = 16, 3.0, 0.1
+    eps, f = si.maxwell_medium(n, n, 0), si.maxwell_point_source(n, n)
+    p = opdes.MaxwellTE2D(nx=n, ny=n, k=k, chi3=chi, eps_r=eps, f=f)
+    lp = J.make_problem("maxwell", n, n, 0.0, 1.0, (k, chi), eps_r=eps, source=f)
+    o = _opts(J, J.JFNK_FP64, lin, "gmres", 60, 1e-8, 1e-8, 50, 30)
+    s, x, rep = _run(J, ctx, lp, o, np.zeros(2 * n * n), 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, oref, bref = onw.bvp_solve(p, _oopts(lin, "gmres", 60, 1e-8, 1e-8, 50, 30))
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-8
+    assert rep.newton_its == oref.newton_its
+
+
+def test_already_converged_start(J, ctx):
+    """u = 0 is a steady state of Allen-Cahn: F(x*) = 0, zero Newton iterations."""
+    n = 16
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64), np.zeros(n * n), 3)
+    assert s == J.JFNK_OK and rep.newton_its == 0 and rep.steps_done == 3
+    assert (x == 0).all()
+
+
+def test_deterministic_and_host_buffers(J, ctx):
+    n = 64
+    u0 = si.allen_cahn_ic(n, n, 9)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    o = _opts(J, J.JFNK_MIXED_FP32, restart=40, tol_n=1e-8, tol_k=1e-5)
+    _, x1, r1 = _run(J, ctx, lp, o, u0, 2)
+    _, x2, r2 = _run(J, ctx, lp, o, u0, 2)
+    assert (x1 == x2).all() and r1.krylov_its == r2.krylov_its
+    # host (numpy) arrays through the same call
+    xh = u0.copy()
+    rep = J.jfnk_report()
+    J.check(ctx, J.jfnk_solve(ctx, o, None, xh, 2, rep), "solve host")
+    assert (xh == x1).all()
+
+
+def test_max_restart_and_invalid_options(J, ctx):
+    n = 48
+    u0 = si.allen_cahn_ic(n, n, 2)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, restart=64), u0, 1)
+    assert s == J.JFNK_OK
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts(restart=64))
+    _compare(x, x_ref, rep, reps, 1e-10)
+    bad = _opts(J, J.JFNK_FP64, restart=65)
+    xt = torch.tensor(u0, device="cuda")
+    assert J.jfnk_solve(ctx, bad, None, xt, 1, None) == J.JFNK_E_INVALID
+    bad = _opts(J, J.JFNK_MIXED_BF16, krylov="bicgstab")
+    assert J.jfnk_solve(ctx, bad, None, xt, 1, None) == J.JFNK_E_INVALID
+    assert J.jfnk_solve(ctx, _opts(J, J.JFNK_FP64), None, xt, 0, None) == J.JFNK_E_INVALID
+
+
+def test_hbm_budget_is_enforced(J):
+    c = J.jfnk_create(0, 1 << 20)
+    try:
+        n = 512
+        J.check(c, J.jfnk_set_problem(c, J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))), "set")
+        xt = torch.zeros(n * n, dtype=torch.float64, device="cuda")
+        assert J.jfnk_solve(c, _opts(J, J.JFNK_FP64), None, xt, 1, None) == J.JFNK_E_OOM
+        assert "budget" in J.jfnk_last_error(c)
+    finally:
+        J.jfnk_destroy(c)
