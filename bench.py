@@ -1,0 +1,363 @@
+"""Benchmark: Newton solves/s of the JFNK hot path on the Allen-Cahn 2048^2 workload.
+
+One benchmark step is one implicit time step of the 2D Allen-Cahn equation
+(u_t = D lap u + u - u^3, periodic 2048 x 2048 grid, D = 1e-3, dt = 0.1,
+Crank-Nicolson, u0 ~ U[-0.1, 0.1] from seed 0), solved by Newton with
+backtracking line search and GMRES(40) whose operator is the forward-mode AD
+JVP. K timed steps advance the trajectory from u0 (K = 10 is the workload's
+ten implicit steps); W warm-up steps solve step 1 and are discarded.
+
+Headline form: mixed precision (FP32 JVP sweeps and Krylov basis, FP64 Newton
+residual, update, line search and Hessenberg). The plain per-solve FP64 AD
+form is measured in the same run for comparison. All compute runs in
+libjfnk's CUDA kernels through its C ABI; this script only allocates device
+memory, times, and prints one JSON line.
+
+Also reported: per-step p50/p99 latency, Newton/Krylov counts, the
+dominant kernel's achieved HBM bandwidth against the measured peak, the
+end-to-end rate through the C ABI with host buffers, the CPU oracle timed on
+a bounded sample (--impl reference runs only that), and SM clocks sampled
+during the timed region.
+
+Multi-GPU (torchrun): the path does not shard; every rank solves its own
+replica of the workload (weak scaling), value = all ranks' solves / max time.
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import math
+import os
+import subprocess
+import sys
+import tempfile
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "Newton solves/s and JVP HBM GB/s (% peak): served FP32 vs plain FP64; p50/p99"
+N_GRID = 2048
+D_COEF, DT, THETA, SEED = 1e-3, 0.1, 0.5, 0
+RESTART = 40
+TOL_NEWTON = 1e-8
+TOL_KRYLOV = {"mixed": 1e-6, "fp64": 1e-8}
+WORKLOAD = "allen_cahn_2048x2048_cn_dt0.1_D1e-3_seed0"
+GOLDEN = os.path.join(ROOT, "tests", "golden", "allen_cahn_2048_step1.json")
+TRAFFIC = os.path.join(ROOT, "profiles", "ncu_traffic.json")
+
+
+def _args():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--cpu-sample-iters", type=int, default=8)
+    ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
+    ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    return ap.parse_args()
+
+
+# ------------------------------------------------------------------------------------------------
+# CPU oracle sample (run in a child process, single-threaded BLAS)
+# ------------------------------------------------------------------------------------------------
+_CPU_SAMPLE = r"""
+import json, sys, time
+sys.path.insert(0, {root!r})
+import numpy as np
+import synthetic_inputs as si
+from oracle import jvp as ojvp, krylov as okr, pdes as opdes
+n, iters = {n}, {iters}
+p = opdes.AllenCahn2D(nx=n, ny=n, D={D}, dt={dt}, theta={theta})
+u0 = si.allen_cahn_ic(n, n, {seed})
+b = p.rhs(u0)
+t = time.perf_counter(); F = p.residual(u0, b); t_res = time.perf_counter() - t
+A = lambda v: ojvp.jvp_complex_step(lambda z: p.residual(z, b), u0, v)[1]
+t = time.perf_counter(); okr.gmres(A, -F, iters, 0.0, 1); t_gm = time.perf_counter() - t
+print(json.dumps({{"t_res": t_res, "t_iter": t_gm / iters, "iters": iters}}))
+"""
+
+
+def cpu_oracle_sample(iters: int) -> dict:
+    env = dict(os.environ, OMP_NUM_THREADS="1", OPENBLAS_NUM_THREADS="1", MKL_NUM_THREADS="1",
+               CUDA_VISIBLE_DEVICES="")
+    code = _CPU_SAMPLE.format(root=ROOT, n=N_GRID, iters=iters, D=D_COEF, dt=DT, theta=THETA, seed=SEED)
+    r = subprocess.run([sys.executable, "-c", code], capture_output=True, text=True, env=env, timeout=900)
+    if r.returncode != 0:
+        raise RuntimeError("oracle sample failed: " + r.stderr[-2000:])
+    return json.loads(r.stdout.strip().splitlines()[-1])
+
+
+def cpu_baseline(iters: int) -> dict:
+    """Oracle solves/s on this host, scaled from a bounded sample by the oracle's own counts."""
+    if not os.path.exists(GOLDEN):
+        return {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                "sample": "unavailable: tests/golden/allen_cahn_2048_step1.json missing"}
+    g = json.load(open(GOLDEN))
+    s = cpu_oracle_sample(iters)
+    n_res = 1 + g["newton_its"] + g["ls_backtracks"]
+    sec = g["krylov_its"] * s["t_iter"] + n_res * s["t_res"]
+    return {"value": 1.0 / sec, "unit": "solves/s", "cores": 1, "kind": "oracle",
+            "sample": (f"numpy FP64 oracle, 1 thread: {iters} GMRES(40) Arnoldi steps with complex-step JVPs "
+                       f"and one residual on the 2048^2 step-1 system ({s['t_iter']:.3f} s/step, "
+                       f"{s['t_res']:.3f} s/residual), scaled by the oracle's own counts for that solve "
+                       f"({g['krylov_its']} Krylov steps, {n_res} residuals)"),
+            "seconds_per_solve": sec}
+
+
+# ------------------------------------------------------------------------------------------------
+# clocks
+# ------------------------------------------------------------------------------------------------
+class Clocks:
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.f = tempfile.NamedTemporaryFile("w+", suffix=".csv", delete=False)
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(index), "--query-gpu=" + self.Q,
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=self.f, stderr=subprocess.DEVNULL)
+        except OSError:
+            self.p = None
+
+    def stop(self) -> dict:
+        if self.p is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.p.terminate()
+        try:
+            self.p.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+        self.f.seek(0)
+        rows = [ln.split(",") for ln in self.f.read().splitlines() if ln.strip()]
+        os.unlink(self.f.name)
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for r in rows:
+            try:
+                sm.append(float(r[1]))
+                smax = float(r[2])
+                for k, nm in enumerate(names):
+                    if r[5 + k].strip().lower() == "active":
+                        reasons.add(nm)
+            except (ValueError, IndexError):
+                continue
+        sm.sort()
+        return {"sm_mhz": sm[len(sm) // 2] if sm else None, "sm_max_mhz": smax, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ------------------------------------------------------------------------------------------------
+def _peaks():
+    try:
+        return json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))
+    except OSError:
+        return None
+
+
+def _src_hash() -> str:
+    h = hashlib.sha256()
+    csrc = os.path.join(ROOT, "paper_2605_13378_gb300", "csrc")
+    for f in sorted(os.listdir(csrc)):
+        h.update(open(os.path.join(csrc, f), "rb").read())
+    return h.hexdigest()[:16]
+
+
+def run_reference(a) -> None:
+    """The oracle as it stands on this host's cores, one bounded sample per step."""
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    for _ in range(a.warmup):
+        cpu_oracle_sample(2)
+    vals = []
+    t0 = time.perf_counter()
+    last = None
+    for _ in range(a.steps):
+        last = cpu_baseline(2)
+        vals.append(last["seconds_per_solve"] if last["value"] else float("nan"))
+    wall = time.perf_counter() - t0
+    sec = sum(vals) / len(vals)
+    value = 1.0 / sec if sec == sec else None
+    out = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": a.gpus,
+           "steps": a.steps, "warmup": a.warmup, "ms_per_step": sec * 1e3, "higher_is_better": True,
+           "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+           "config": {"workload": WORKLOAD, "solver": "Newton + GMRES(40), AD (complex step), FP64 oracle"},
+           "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle",
+                            "sample": last["sample"] if last else None},
+           "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+           "wall_s": wall}
+    print(json.dumps(out))
+
+
+def main() -> None:
+    a = _args()
+    if a.impl == "reference":
+        run_reference(a)
+        return
+    import torch
+
+    import synthetic_inputs as si
+    from paper_2605_13378_gb300 import jfnk as J
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl")
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def max_over_ranks(v: float) -> float:
+        if dist is None:
+            return v
+        t = torch.tensor([v], device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        return float(t.item())
+
+    stream = torch.cuda.Stream()
+    ctx = J.jfnk_create(local, 0, stream.cuda_stream)
+    J.check(ctx, J.jfnk_set_problem(ctx, J.make_problem("allen_cahn", N_GRID, N_GRID, DT, THETA, (D_COEF, 1.0))),
+            "set_problem")
+    u0 = si.allen_cahn_ic(N_GRID, N_GRID, SEED)
+    u0_dev = torch.tensor(u0, device="cuda")
+    x = torch.empty_like(u0_dev)
+
+    def opts(form):
+        o = J.jfnk_default_opts(J.JFNK_MIXED_FP32 if form == "mixed" else J.JFNK_FP64)
+        o.restart, o.tol_newton, o.tol_krylov = RESTART, TOL_NEWTON, TOL_KRYLOV[form]
+        o.max_newton, o.max_krylov = 15, 100
+        return o
+
+    def run_steps(form, k, timing=False):
+        """k trajectory steps from u0; returns (event ms per step, reports, final x)."""
+        o = opts(form)
+        J.jfnk_set_timing(ctx, timing)
+        x.copy_(u0_dev)
+        evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
+        reps = []
+        barrier()
+        with torch.cuda.stream(stream):
+            evs[0].record(stream)
+            for s in range(k):
+                rep = J.jfnk_report()
+                st = J.jfnk_solve(ctx, o, None, x, 1, rep)
+                if st not in (J.JFNK_OK, J.JFNK_E_NOT_CONVERGED):
+                    raise RuntimeError(J.jfnk_status_string(st) + ": " + J.jfnk_last_error(ctx))
+                evs[s + 1].record(stream)
+                reps.append(rep.as_dict())
+        barrier()
+        J.jfnk_set_timing(ctx, False)
+        return [evs[s].elapsed_time(evs[s + 1]) for s in range(k)], reps, x.clone()
+
+    # warm-up: step 1 solved W times
+    o_m = opts("mixed")
+    for _ in range(a.warmup):
+        x.copy_(u0_dev)
+        torch.cuda.synchronize()
+        J.check(ctx, J.jfnk_solve(ctx, o_m, None, x, 1, None), "warmup")
+    torch.cuda.synchronize()
+
+    # timed region: K steps, device events on the library's stream
+    clocks = Clocks(local)
+    J.jfnk_reset_stats(ctx)
+    ms, reps, x_mixed = run_steps("mixed", a.steps)
+    clk = clocks.stop()
+    gpu_launches = J.jfnk_kernel_stats(ctx)["all_launches"]["launches"]
+    total_ms = max_over_ranks(sum(ms))
+    value = world * a.steps / (total_ms / 1e3)
+    srt = sorted(ms)
+    p50 = srt[len(srt) // 2]
+    p99 = srt[min(len(srt) - 1, int(math.ceil(0.99 * len(srt))) - 1)]
+
+    # per-kernel device times: the same steps again with events around every launch
+    J.jfnk_reset_stats(ctx)
+    ms_t, _, _ = run_steps("mixed", a.steps, timing=True)
+    stats = J.jfnk_kernel_stats(ctx)
+    stats.pop("all_launches", None)
+    ktot = sum(v["ms"] for v in stats.values())
+    kern = {k: {"launches": v["launches"], "ms": round(v["ms"], 3),
+                "share": round(v["ms"] / ktot, 4) if ktot else 0.0,
+                "gbs": round(v["bytes"] / (v["ms"] * 1e-3) / 1e9, 1) if v["ms"] else None}
+            for k, v in stats.items() if v["launches"]}
+    dom = max(kern, key=lambda k: kern[k]["ms"])
+    peaks = _peaks()
+    peak = peaks["hbm_gbs"] if peaks else 6800.0
+    ach = kern[dom]["gbs"]
+    traffic = None
+    if os.path.exists(TRAFFIC):
+        tr = json.load(open(TRAFFIC))
+        if tr.get("src_hash") == _src_hash() and dom in tr.get("kernels", {}):
+            traffic = tr["kernels"][dom]["dram_bytes_per_launch"]
+    roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
+                "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,
+                "peak_source": "measured" if peaks else "fallback",
+                "bytes_per_launch": stats[dom]["bytes"] / stats[dom]["launches"]}
+    jv = stats.get("jvp_ad", {"ms": 0})
+    jvp_gbs = jv["bytes"] / (jv["ms"] * 1e-3) / 1e9 if jv.get("ms") else None
+
+    # plain per-solve FP64 AD form, same steps
+    fp64 = None
+    if not a.no_fp64:
+        ms64, reps64, x64 = run_steps("fp64", a.steps)
+        fp64 = {"value": world * a.steps / (max_over_ranks(sum(ms64)) / 1e3), "unit": "solves/s",
+                "ms_per_step": sum(ms64) / a.steps, "p50_ms": sorted(ms64)[len(ms64) // 2],
+                "newton_its": sum(r["newton_its"] for r in reps64),
+                "krylov_its": sum(r["krylov_its"] for r in reps64),
+                "max_rel_diff_mixed_vs_fp64": float((x_mixed - x64).abs().max() / x64.abs().max())}
+
+    # end to end through the C ABI with host buffers: H2D of each step's input, D2H of its result
+    e2e = None
+    if not a.no_e2e:
+        pin_in = torch.empty(u0.size, dtype=torch.float64, pin_memory=True)
+        pin_out = torch.empty_like(pin_in)
+        pin_in.copy_(torch.from_numpy(u0))
+        J.check(ctx, J.jfnk_solve(ctx, o_m, pin_in, pin_out, 1, None), "e2e warmup")
+        barrier()
+        t0 = time.perf_counter()
+        for _ in range(a.steps):
+            J.check(ctx, J.jfnk_solve(ctx, o_m, pin_in, pin_out, 1, None), "e2e")
+            pin_in.copy_(pin_out)
+        barrier()
+        e2e_s = max_over_ranks(time.perf_counter() - t0)
+        e2e = {"value": world * a.steps / e2e_s, "unit": "solves/s", "h2d_bytes_per_step": u0.size * 8,
+               "d2h_bytes_per_step": u0.size * 8}
+
+    cpu = cpu_baseline(a.cpu_sample_iters) if (rank == 0 and world == 1 and not a.no_cpu) else None
+    J.jfnk_destroy(ctx)
+    if rank != 0:
+        return
+    out = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": world, "steps": a.steps,
+        "warmup": a.warmup, "ms_per_step": total_ms / a.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32+f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "steps_per_run": a.steps,
+                   "form": "mixed: FP32 AD JVP + FP32 GMRES(40) basis, FP64 Newton residual/update/line search/"
+                           "Hessenberg", "tol_newton": TOL_NEWTON, "tol_krylov": TOL_KRYLOV["mixed"],
+                   "l2": "inputs larger than L2 (GMRES basis 656 MB, state 32 MB per vector)",
+                   "parallelism": f"replicas x{world}"},
+        "p50_ms": p50, "p99_ms": p99,
+        "newton_its": sum(r["newton_its"] for r in reps), "krylov_its": sum(r["krylov_its"] for r in reps),
+        "jvp_gbs": jvp_gbs, "jvp_frac": (jvp_gbs / peak) if jvp_gbs else None,
+        "fp64_plain": fp64, "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches,
+        "timed_with_kernel_events_ms_per_step": sum(ms_t) / a.steps,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+    }
+    print(json.dumps(out))
+
+
+if __name__ == "__main__":
+    main()

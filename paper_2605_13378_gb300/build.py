@@ -19,7 +19,8 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libjfnk.so")
-SOURCES = ["stencil.cu", "krylov.cu", "jfnk.cu", "serve.cu"]
+SOURCES = ["stencil.cu", "stencil_burgers.cu", "stencil_allen_cahn.cu", "stencil_su_olson.cu", "stencil_maxwell.cu",
+           "krylov.cu", "jfnk.cu", "serve.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC,-O2",
          "-I" + INCLUDE, "-I" + CSRC]

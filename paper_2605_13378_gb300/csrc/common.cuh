@@ -101,8 +101,9 @@ template <class A> __device__ __forceinline__ A warp_sum(A v) {
 // that the last block resets to zero.
 template <class A>
 struct RedSite {
-  A* partials;            // [nblocks][kMaxK]
+  A* partials;            // [cap][kMaxK]
   unsigned int* counter;  // one word, zero between launches
+  int cap;                // capacity of partials in blocks
 };
 
 // Block-level reduction of k values per thread (k <= KMAX, same k in all
@@ -118,6 +119,7 @@ __device__ __forceinline__ bool grid_reduce(A (&vals)[KMAX], int k, RedSite<A> s
   const int tid = threadIdx.x + threadIdx.y * blockDim.x;
   const int nthr = blockDim.x * blockDim.y;
   const int lane = tid & 31, warp = tid >> 5, nwarps = nthr >> 5;
+  if (nblocks > site.cap) return false;   // host sizing error: never write past the partials
 #pragma unroll
   for (int t = 0; t < KMAX; ++t) {
     if (t < k) {

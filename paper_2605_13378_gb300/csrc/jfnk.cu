@@ -14,6 +14,7 @@
 #include <chrono>
 #include <cmath>
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 #include <vector>
@@ -46,6 +47,7 @@ struct Pending {
 
 struct Timer {
   bool on = false;
+  long long total_launches = 0;   // every kernel launched by the solver, timed or not
   std::vector<cudaEvent_t> pool;
   int used = 0;
   std::vector<Pending> pending;
@@ -81,6 +83,9 @@ struct jfnk_ctx {
   double* src64 = nullptr; float* src32 = nullptr;
   // small permanent device state
   double* dsc = nullptr;          // scalar slots
+  unsigned int* derr = nullptr;   // device error word (bounded waits that expired)
+  int nsm = 0;                    // multiprocessors: grid of the streaming kernels
+  bool stream_ok = true;          // bulk-copy streaming of the basis allowed (JFNK_NO_STREAM=1 disables)
   GmresCtl* gctl = nullptr;
   BicgCtl* bctl = nullptr;
   RedWs red{};
@@ -148,8 +153,9 @@ void ws_free(jfnk_ctx* ctx) {
 // --------------------------------------------------------------------------
 // timing
 // --------------------------------------------------------------------------
-int tm_begin(jfnk_ctx* ctx, int cls, double bytes, int tag) {
+int tm_begin(jfnk_ctx* ctx, int cls, double bytes, int tag, int nkernels = 1) {
   Timer& t = ctx->tm;
+  t.total_launches += nkernels;
   if (!t.on) return -1;
   if (t.used + 2 > (int)t.pool.size()) {
     for (int q = 0; q < 64; ++q) {
@@ -174,7 +180,7 @@ void tm_harvest(jfnk_ctx* ctx, int valid, double fin_bytes) {
   Timer& t = ctx->tm;
   if (!t.on) return;
   for (const Pending& p : t.pending) {
-    if (p.tag >= 0 && p.tag >= valid) continue;
+    if (p.tag == -2 || (p.tag >= 0 && p.tag >= valid)) continue;
     float ms = 0.f;
     if (cudaEventElapsedTime(&ms, t.pool[p.ev], t.pool[p.ev + 1]) != cudaSuccess) { cudaGetLastError(); continue; }
     t.launches[p.cls] += 1;
@@ -220,9 +226,10 @@ jfnk_status ensure_ws(jfnk_ctx* ctx, int prec, int m, int krylov) {
 
 jfnk_status ensure_red(jfnk_ctx* ctx) {
   int need = vec_blocks(ctx->N);
+  if (ctx->nsm > need) need = ctx->nsm;   // grid of the streaming kernels
   if (ctx->have_prob) {
     const StencilGeom g = stencil_geom(ctx->P);
-    if (g.nblocks > need) need = g.nblocks;
+    if (g.max_blocks > need) need = g.max_blocks;
   }
   if (need <= ctx->red_cap_blocks) return JFNK_OK;
   if (ctx->red.partials) { cudaFree(ctx->red.partials); ctx->allocated -= (size_t)ctx->red_cap_blocks * kMaxK * 8; }
@@ -314,6 +321,7 @@ struct Solver {
     jfnk_ctx::Ws& w = ctx->ws;
     const int m = o.restart;
     const double nv = (double)N;
+    const bool streamed = ctx->stream_ok && stream_supported(N);
     *ctx->hflag = 1;   // before any launch that may clear it
     int ev = tm_begin(ctx, KC_GINIT, nv * (ss() + sb() + sj() + ss()), -1);
     cudaError_t e = launch_gmres_init(ts, tj, tb, td, N, F, w.V, w.rhsk, w.d, ctx->gctl, sc, o.tol_krylov, m,
@@ -376,7 +384,11 @@ struct Solver {
         for (int pass = 1; pass <= 3; ++pass) {
           const double bytes = bs + nv * sj() * (pass == 2 ? 2 : 1) + (pass == 3 ? nv * sb() : 0.0);
           int ev3 = tm_begin(ctx, KC_ARN1 + pass - 1, bytes, j);
-          e = launch_arnoldi_pass(pass, tb, tj, N, w.V, k, w.w, ctx->gctl, ctx->red, ctx->stream);
+          if (streamed)
+            e = launch_basis_stream(pass, tb, tj, td, N, w.V, k, k, w.w, nullptr, ctx->gctl, ctx->red, ctx->derr,
+                                    ctx->nsm, ctx->stream);
+          else
+            e = launch_arnoldi_pass(pass, tb, tj, N, w.V, k, w.w, ctx->gctl, ctx->red, ctx->stream);
           tm_end(ctx, ev3);
           if (e != cudaSuccess) return cuda_fail(ctx, e, "arnoldi kernel");
         }
@@ -384,15 +396,21 @@ struct Solver {
         launched = k;
       }
       if (launched > 0) {
-        int ev4 = tm_begin(ctx, KC_GFIN, 0.0, -1);
-        e = launch_gmres_finish(tb, td, N, w.V, w.d, ctx->gctl, launched, ctx->stream);
+        int ev4 = tm_begin(ctx, KC_GFIN, 0.0, -1, 2);
+        e = launch_gmres_finish(tb, td, N, w.V, w.d, ctx->gctl, launched, ctx->stream, streamed ? 1 : 0, ctx->derr,
+                                ctx->nsm);
         tm_end(ctx, ev4);
         if (e != cudaSuccess) return cuda_fail(ctx, e, "gmres update");
       }
+      CK(cudaMemcpyAsync((char*)ctx->hbuf + 8192, ctx->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream),
+         "read-back");
       jfnk_status s = sync_read(ctx->gctl, kGmresHeadBytes);
       if (s) return s;
       GmresCtl head;
       std::memcpy(&head, ctx->hbuf, kGmresHeadBytes);
+      unsigned derr = 0;
+      std::memcpy(&derr, (char*)ctx->hbuf + 8192, sizeof(unsigned));
+      if (derr) return fail(ctx, JFNK_E_TIMEOUT, "a bounded wait on a bulk copy expired in the Arnoldi kernels");
       tm_harvest(ctx, head.k, (double)head.k * nv * sb() + 2.0 * nv * vt_size(td));
       rep.jvp_calls += head.k + (cycle > 0 ? 1 : 0);
       if (head.nonfinite) { rep.krylov_its += head.its; *kstatus = JFNK_E_NONFINITE; return JFNK_OK; }
@@ -435,7 +453,9 @@ struct Solver {
       e = launch_bicg(2, ts, tj, td, N, vv, ctx->bctl, ctx->red, it, o.tol_krylov, ctx->stream);
       tm_end(ctx, e2);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "bicgstab s");
+      int e4 = tm_begin(ctx, KC_BICG, 0.0, -2);
       e = launch_bicg(3, ts, tj, td, N, vv, ctx->bctl, ctx->red, it, o.tol_krylov, ctx->stream);
+      tm_end(ctx, e4);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "bicgstab half");
       JvpArgs b2 = jvp_base();
       b2.v = w.s; b2.out = w.t; b2.ndots = 2; b2.dw[0] = w.s; b2.dw[1] = nullptr; b2.sums = ctx->bctl->sums;
@@ -546,8 +566,13 @@ static jfnk_status jfnk_create_impl(jfnk_ctx* ctx, int device, size_t hbm_budget
   if ((s = dalloc(ctx, (void**)&ctx->dsc, 64 * sizeof(double), nullptr)) ||
       (s = dalloc(ctx, (void**)&ctx->gctl, sizeof(GmresCtl), nullptr)) ||
       (s = dalloc(ctx, (void**)&ctx->bctl, sizeof(BicgCtl), nullptr)) ||
-      (s = dalloc(ctx, (void**)&ctx->red.counter, 256, nullptr)))
+      (s = dalloc(ctx, (void**)&ctx->red.counter, 256, nullptr)) ||
+      (s = dalloc(ctx, (void**)&ctx->derr, 256, nullptr)))
     return s;
+  CK(cudaMemset(ctx->derr, 0, 256), "memset");
+  CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device), "device attribute");
+  const char* ns = std::getenv("JFNK_NO_STREAM");
+  ctx->stream_ok = !(ns && ns[0] == '1');
   CK(cudaMemset(ctx->dsc, 0, 64 * sizeof(double)), "memset");
   CK(cudaMemset(ctx->gctl, 0, sizeof(GmresCtl)), "memset");
   CK(cudaMemset(ctx->bctl, 0, sizeof(BicgCtl)), "memset");
@@ -630,7 +655,7 @@ void jfnk_destroy(jfnk_ctx* ctx) {
   ws_free(ctx);
   cudaFree(ctx->eps64); cudaFree(ctx->eps32); cudaFree(ctx->src64); cudaFree(ctx->src32);
   cudaFree(ctx->dsc); cudaFree(ctx->gctl); cudaFree(ctx->bctl);
-  cudaFree(ctx->red.partials); cudaFree(ctx->red.counter); cudaFree(ctx->jscratch);
+  cudaFree(ctx->red.partials); cudaFree(ctx->red.counter); cudaFree(ctx->jscratch); cudaFree(ctx->derr);
   if (ctx->hflag) cudaFreeHost((void*)ctx->hflag);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
   for (int q = 0; q <= kLookahead; ++q) if (ctx->iter_ev[q]) cudaEventDestroy(ctx->iter_ev[q]);
@@ -857,7 +882,9 @@ jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_pre
   } else {
     for (int step = 0; step < steps; ++step) {
       // x^n -> b_n; x starts from x^n
+      const int evr = tm_begin(ctx, KC_RHS, (double)N * 2 * vt_size(sv.ts), -1);
       cudaError_t e = launch_rhs(sv.P, sv.ts, sv.x, w.b, ctx->stream);
+      tm_end(ctx, evr);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "rhs kernel");
       if (sv.tj != sv.ts) {
         s = sv.cast(sv.ts, sv.tj, w.b, w.b32, 1.0);
@@ -907,12 +934,20 @@ int jfnk_kernel_stats(jfnk_ctx* ctx, const char** names, long long* launches, do
     if (total_ms) total_ms[n] = ctx->tm.ms[c];
     if (bytes) bytes[n] = ctx->tm.bytes[c];
   }
+  if (n < cap) {   // every launch, including those a converged Krylov loop turned into no-ops
+    if (names) names[n] = "all_launches";
+    if (launches) launches[n] = ctx->tm.total_launches;
+    if (total_ms) total_ms[n] = 0.0;
+    if (bytes) bytes[n] = 0.0;
+    ++n;
+  }
   return n;
 }
 
 void jfnk_reset_stats(jfnk_ctx* ctx) {
   if (!ctx) return;
   for (int c = 0; c < KC_COUNT; ++c) { ctx->tm.launches[c] = 0; ctx->tm.ms[c] = 0; ctx->tm.bytes[c] = 0; }
+  ctx->tm.total_launches = 0;
 }
 
 jfnk_status jfnk_submit(jfnk_ctx* ctx, const jfnk_problem* prob, const jfnk_opts* opts, const double* x0,

@@ -32,6 +32,7 @@ struct StencilGeom {
   dim3 block, grid;
   int rows_per_thread;     // R: each thread handles R rows strided by blockDim.y
   int nblocks;             // grid.x * grid.y
+  int max_blocks;          // largest grid of any stencil launch form of the problem (reduction capacity)
 };
 StencilGeom stencil_geom(const ProbDev& P);
 

@@ -23,6 +23,13 @@ cudaError_t launch_gmres_init(int ts, int tj, int tb, int td, long long n, const
                               void* d, GmresCtl* ctl, const double* sums, double tol, int m, cudaStream_t st);
 // back substitution + d += V y over at most kmax vectors
 cudaError_t launch_gmres_finish(int tb, int td, long long n, const void* V, void* d, GmresCtl* ctl, int kmax,
+                                cudaStream_t st, int streamed, unsigned int* err, int nsm);
+// Streaming (bulk-copy) form of the basis passes: mode 1 dots, 2 update + dots,
+// 3 update + norm + Givens (Arnoldi step k - 1), 4 solution update d += V y
+// over ctl->k vectors (kmax an upper bound known to the host). nsm CTAs.
+bool stream_supported(long long n);
+cudaError_t launch_basis_stream(int mode, int tb, int tj, int td, long long n, const void* V, int k, int kmax,
+                                void* w, void* d, GmresCtl* ctl, RedWs red, unsigned int* err, int nsm,
                                 cudaStream_t st);
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);
 cudaError_t launch_vdots(int t, long long n, int nd, const void* const* a, const void* const* b, double* sums,

@@ -1,11 +1,15 @@
 // pdes.cuh -- per-cell discrete residuals of the four benchmark PDEs.
 //
-// Each PDE is a struct with a static `cell` function that, given a loader
-// (flat index -> value) and a cell (i, j), returns for every field f the
-// "mass" term M_f(x) and the spatial operator G_f(x) at that cell. The value
-// type V is a plain float/double (residual, FD quotient) or a Dual (AD JVP):
-// the same source computes F(x) and, on dual numbers, J(x) v (Eq. 9).
-// Branches test primal values only, so AD differentiates the branch taken.
+// Each PDE is a struct with a static `cell` function that, given the values
+// of the 3 x 3 neighbourhood of cell (i, j) for every field, returns per
+// field the "mass" term M_f(x) and the spatial operator G_f(x) at that cell.
+// Values outside the grid are supplied by the PDE's boundary policy (periodic
+// wrap or clamp to the wall cell); walls with other conditions (the Marshak
+// and zero-flux faces of the radiation problem, the absorbing ghosts of the
+// Maxwell problem) are handled inside `cell` from (i, j). The value type V is
+// a plain float/double (residual, FD quotient) or a Dual (AD JVP): the same
+// source computes F(x) and, on dual numbers, J(x) v (Eq. 9). Branches test
+// primal values only, so AD differentiates the branch taken.
 //
 // The theta-method residual of an implicit step (Eq. 2) is assembled by the
 // caller as F = M - theta dt G - b; the Maxwell problem is a boundary-value
@@ -21,13 +25,13 @@ namespace jfnk {
 struct ProbDev {
   int pde, nx, ny, nf;
   long long ncell;        // nx * ny
-  double thdt;            // theta * dt (1 for the boundary-value problem, unused)
+  double thdt;            // theta * dt (unused by the boundary-value problem)
   double c_old;           // (1 - theta) * dt
   double invhx, invhy, invhx2, invhy2;
   double p0, p1, p2, p3;  // PDE parameters (see jfnk_pde)
   int flag;               // Su-Olson: flux limiter on
   int bvp;
-  // Su-Olson Marshak wall: q = mq_a - mq_b * E_0
+  // Su-Olson Marshak wall: inward flux q = mq_a - mq_b * E_0
   double mq_a, mq_b;
   // Maxwell first-order absorbing wall: E_ghost = (cr + i ci) E_wall
   double cxr, cxi, cyr, cyi;
@@ -42,6 +46,22 @@ template <class T> __device__ __forceinline__ const T* src_of(const ProbDev& P);
 template <> __device__ __forceinline__ const double* src_of<double>(const ProbDev& P) { return P.src64; }
 template <> __device__ __forceinline__ const float* src_of<float>(const ProbDev& P) { return P.src32; }
 
+enum BoundaryPolicy { BP_WRAP = 0, BP_CLAMP = 1 };
+
+// Neighbourhood of one cell: centre, the four face neighbours and the four
+// corner neighbours (corners only for PDEs with DIAG) of each field.
+template <class V, int NF>
+struct Nb {
+  V c[NF], e[NF], w[NF], n[NF], s[NF];
+  V ne[NF], nw[NF], se[NF], sw[NF];
+};
+
+// Per-cell coefficients read from problem arrays (Maxwell: eps_r, source).
+template <class T>
+struct CellAux {
+  T eps, fr, fi;
+};
+
 // ---------------------------------------------------------------------------
 // 1D viscous Burgers, periodic, cells x_i = i/N. Conservative upwind flux
 // Phi_{i+1/2} = u_i^2/2 if u_i + u_{i+1} >= 0 else u_{i+1}^2/2 (the Roe flux),
@@ -50,18 +70,18 @@ template <> __device__ __forceinline__ const float* src_of<float>(const ProbDev&
 // ---------------------------------------------------------------------------
 struct Burgers1D {
   static constexpr int NF = 1;
-  template <class T, class V, class L>
-  __device__ __forceinline__ static void cell(const ProbDev& P, const L& ld, int i, int /*j*/, V* M, V* G) {
-    const int n = P.nx;
-    const int im = (i == 0) ? n - 1 : i - 1;
-    const int ip = (i == n - 1) ? 0 : i + 1;
-    V u = ld(i), um = ld(im), up = ld(ip);
+  static constexpr bool DIAG = false;
+  static constexpr int POLICY = BP_WRAP;
+  static constexpr bool AUX = false;
+  template <class T, class V>
+  __device__ __forceinline__ static void cell(const ProbDev& P, int, int, const Nb<V, 1>& q, const CellAux<T>&,
+                                              V* M, V* G) {
+    const V u = q.c[0], um = q.w[0], up = q.e[0];
     const T half = T(0.5);
     V phip = (primal(u) + primal(up) >= T(0)) ? half * u * u : half * up * up;
     V phim = (primal(um) + primal(u) >= T(0)) ? half * um * um : half * u * u;
-    const T invh = T(P.invhx), invh2 = T(P.invhx2), nu = T(P.p0);
     M[0] = u;
-    G[0] = (phim - phip) * invh + nu * ((up - T(2) * u + um) * invh2);
+    G[0] = (phim - phip) * T(P.invhx) + T(P.p0) * ((up - T(2) * u + um) * T(P.invhx2));
   }
 };
 
@@ -71,16 +91,14 @@ struct Burgers1D {
 // ---------------------------------------------------------------------------
 struct AllenCahn2D {
   static constexpr int NF = 1;
-  template <class T, class V, class L>
-  __device__ __forceinline__ static void cell(const ProbDev& P, const L& ld, int i, int j, V* M, V* G) {
-    const int nx = P.nx, ny = P.ny;
-    const int ie = (i == nx - 1) ? 0 : i + 1, iw = (i == 0) ? nx - 1 : i - 1;
-    const int jn = (j == ny - 1) ? 0 : j + 1, js = (j == 0) ? ny - 1 : j - 1;
-    const long long r = (long long)j * nx;
-    V u = ld(r + i);
-    V ue = ld(r + ie), uw = ld(r + iw);
-    V un = ld((long long)jn * nx + i), us = ld((long long)js * nx + i);
-    V lap = (ue - T(2) * u + uw) * T(P.invhx2) + (un - T(2) * u + us) * T(P.invhy2);
+  static constexpr bool DIAG = false;
+  static constexpr int POLICY = BP_WRAP;
+  static constexpr bool AUX = false;
+  template <class T, class V>
+  __device__ __forceinline__ static void cell(const ProbDev& P, int, int, const Nb<V, 1>& q, const CellAux<T>&,
+                                              V* M, V* G) {
+    const V u = q.c[0];
+    V lap = (q.e[0] - T(2) * u + q.w[0]) * T(P.invhx2) + (q.n[0] - T(2) * u + q.s[0]) * T(P.invhy2);
     M[0] = u;
     G[0] = T(P.p0) * lap + T(P.p1) * u - u * u * u;
   }
@@ -95,9 +113,13 @@ struct AllenCahn2D {
 // touching the face, mirror values beyond a wall), Ebar the mean of the two
 // cells; limiter off: D = 1/(3 sigma). Left wall: inward Marshak flux
 // q = 2 D_b (4 F_inc - E_0)/(h + 4 D_b) = mq_a - mq_b E_0; other walls: no flux.
+// The clamp policy supplies the mirror values.
 // ---------------------------------------------------------------------------
 struct SuOlson2D {
   static constexpr int NF = 2;
+  static constexpr bool DIAG = true;
+  static constexpr int POLICY = BP_CLAMP;
+  static constexpr bool AUX = false;
   template <class T, class V>
   __device__ __forceinline__ static V face_flux(const ProbDev& P, V gn, V gt, V Ebar) {
     const T three_sigma = T(3) * T(P.p0);
@@ -106,36 +128,33 @@ struct SuOlson2D {
     V R = dsqrt((gn * gn + gt * gt) / (Ebar * Ebar) + rho * rho);
     return gn / (three_sigma + R);
   }
-  template <class T, class V, class L>
-  __device__ __forceinline__ static void cell(const ProbDev& P, const L& ld, int i, int j, V* M, V* G) {
+  template <class T, class V>
+  __device__ __forceinline__ static void cell(const ProbDev& P, int i, int j, const Nb<V, 2>& q, const CellAux<T>&,
+                                              V* M, V* G) {
     const int nx = P.nx, ny = P.ny;
-    const int ic0 = i > 0 ? i - 1 : 0, ic2 = i < nx - 1 ? i + 1 : nx - 1;
-    const int jc0 = j > 0 ? j - 1 : 0, jc2 = j < ny - 1 ? j + 1 : ny - 1;
-    const long long r0 = (long long)jc0 * nx, r1 = (long long)j * nx, r2 = (long long)jc2 * nx;
-    // E(a, b): column ic_a, row jc_b
-    V E00 = ld(r0 + ic0), E10 = ld(r0 + i), E20 = ld(r0 + ic2);
-    V E01 = ld(r1 + ic0), E11 = ld(r1 + i), E21 = ld(r1 + ic2);
-    V E02 = ld(r2 + ic0), E12 = ld(r2 + i), E22 = ld(r2 + ic2);
-    V Tc = ld(P.ncell + r1 + i);
-    const T ihx = T(P.invhx), ihy = T(P.invhy), q = T(0.25), half = T(0.5);
+    const V E00 = q.sw[0], E10 = q.s[0], E20 = q.se[0];
+    const V E01 = q.w[0], E11 = q.c[0], E21 = q.e[0];
+    const V E02 = q.nw[0], E12 = q.n[0], E22 = q.ne[0];
+    const V Tc = q.c[1];
+    const T ihx = T(P.invhx), ihy = T(P.invhy), qq = T(0.25), half = T(0.5);
     V fe, fw, fn, fs;
     if (i < nx - 1) {
-      fe = face_flux<T>(P, (E21 - E11) * ihx, ((E12 + E22) - (E10 + E20)) * (q * ihy), half * (E11 + E21));
+      fe = face_flux<T>(P, (E21 - E11) * ihx, ((E12 + E22) - (E10 + E20)) * (qq * ihy), half * (E11 + E21));
     } else {
       fe = V(T(0));
     }
     if (i > 0) {
-      fw = face_flux<T>(P, (E11 - E01) * ihx, ((E02 + E12) - (E00 + E10)) * (q * ihy), half * (E01 + E11));
+      fw = face_flux<T>(P, (E11 - E01) * ihx, ((E02 + E12) - (E00 + E10)) * (qq * ihy), half * (E01 + E11));
     } else {
       fw = E11 * T(P.mq_b) - T(P.mq_a);   // D dE/dx at the wall = -q
     }
     if (j < ny - 1) {
-      fn = face_flux<T>(P, (E12 - E11) * ihy, ((E21 + E22) - (E01 + E02)) * (q * ihx), half * (E11 + E12));
+      fn = face_flux<T>(P, (E12 - E11) * ihy, ((E21 + E22) - (E01 + E02)) * (qq * ihx), half * (E11 + E12));
     } else {
       fn = V(T(0));
     }
     if (j > 0) {
-      fs = face_flux<T>(P, (E11 - E10) * ihy, ((E20 + E21) - (E00 + E01)) * (q * ihx), half * (E10 + E11));
+      fs = face_flux<T>(P, (E11 - E10) * ihy, ((E20 + E21) - (E00 + E01)) * (qq * ihx), half * (E10 + E11));
     } else {
       fs = V(T(0));
     }
@@ -159,33 +178,30 @@ struct SuOlson2D {
 // ---------------------------------------------------------------------------
 struct MaxwellTE2D {
   static constexpr int NF = 2;
-  template <class T, class V, class L>
-  __device__ __forceinline__ static void cell(const ProbDev& P, const L& ld, int i, int j, V* M, V* G) {
+  static constexpr bool DIAG = false;
+  static constexpr int POLICY = BP_CLAMP;
+  static constexpr bool AUX = true;
+  template <class T, class V>
+  __device__ __forceinline__ static void cell(const ProbDev& P, int i, int j, const Nb<V, 2>& q,
+                                              const CellAux<T>& aux, V* M, V* G) {
     const int nx = P.nx, ny = P.ny;
-    const long long n = P.ncell, c = (long long)j * nx + i;
-    V A = ld(c), B = ld(n + c);
+    const V A = q.c[0], B = q.c[1];
     const T cxr = T(P.cxr), cxi = T(P.cxi), cyr = T(P.cyr), cyi = T(P.cyi);
-    V gxA = cxr * A - cxi * B, gxB = cxr * B + cxi * A;   // ghost beyond an x wall
-    V gyA = cyr * A - cyi * B, gyB = cyr * B + cyi * A;   // ghost beyond a y wall
-    V Aw, Bw, Ae, Be, As, Bs, An, Bn;
-    if (i > 0) { Aw = ld(c - 1); Bw = ld(n + c - 1); } else { Aw = gxA; Bw = gxB; }
-    if (i < nx - 1) { Ae = ld(c + 1); Be = ld(n + c + 1); } else { Ae = gxA; Be = gxB; }
-    if (j > 0) { As = ld(c - nx); Bs = ld(n + c - nx); } else { As = gyA; Bs = gyB; }
-    if (j < ny - 1) { An = ld(c + nx); Bn = ld(n + c + nx); } else { An = gyA; Bn = gyB; }
+    const V gxA = cxr * A - cxi * B, gxB = cxr * B + cxi * A;   // ghost beyond an x wall
+    const V gyA = cyr * A - cyi * B, gyB = cyr * B + cyi * A;   // ghost beyond a y wall
+    const V Aw = i > 0 ? q.w[0] : gxA, Bw = i > 0 ? q.w[1] : gxB;
+    const V Ae = i < nx - 1 ? q.e[0] : gxA, Be = i < nx - 1 ? q.e[1] : gxB;
+    const V As = j > 0 ? q.s[0] : gyA, Bs = j > 0 ? q.s[1] : gyB;
+    const V An = j < ny - 1 ? q.n[0] : gyA, Bn = j < ny - 1 ? q.n[1] : gyB;
     const T ihx2 = T(P.invhx2), ihy2 = T(P.invhy2);
     V LA = (Ae - T(2) * A + Aw) * ihx2 + (An - T(2) * A + As) * ihy2;
     V LB = (Be - T(2) * B + Bw) * ihx2 + (Bn - T(2) * B + Bs) * ihy2;
-    const T* epsp = eps_of<T>(P);
-    const T* srcp = src_of<T>(P);
-    const T eps = epsp ? __ldg(epsp + c) : T(1);
-    const T fr = srcp ? __ldg(srcp + c) : T(0);
-    const T fi = srcp ? __ldg(srcp + n + c) : T(0);
     const T k2 = T(P.p0) * T(P.p0), chi = T(P.p1);
-    V coef = k2 * (eps + chi * (A * A + B * B));
+    V coef = k2 * (aux.eps + chi * (A * A + B * B));
     M[0] = A;
     M[1] = B;
-    G[0] = LA + coef * A - fr;
-    G[1] = LB + coef * B - fi;
+    G[0] = LA + coef * A - aux.fr;
+    G[1] = LB + coef * B - aux.fi;
   }
 };
 

@@ -1,0 +1,85 @@
+// stream.cuh -- bulk-copy (TMA) streaming of vector chunks into shared memory.
+//
+// A persistent CTA walks the chunks it owns and keeps S stages of a shared-
+// memory ring in flight. A producer warp arms a stage's "full" mbarrier with
+// the byte count and its lanes issue one cp.async.bulk per vector chunk; the
+// consumer warps wait on that phase, compute from shared memory and arrive on
+// the stage's "empty" mbarrier, after which the producer refills the stage
+// with the chunk S positions ahead. Waits are bounded by the global timer: on
+// expiry the kernel records an error code and stops, so a fault in the copy
+// path cannot hang the device.
+#pragma once
+
+#include <stdint.h>
+
+#include "common.cuh"
+
+namespace jfnk {
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)), "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+__device__ __forceinline__ uint64_t global_timer_ns() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_arrive(uint64_t* bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(bar)) : "memory");
+}
+
+// Wait for phase `parity` of `bar`, at most `limit_ns`; false on expiry.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, uint64_t limit_ns) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const uint64_t t0 = global_timer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// Bulk copy global -> shared, completing `bytes` on `bar` (16-byte aligned
+// addresses, bytes a multiple of 16).
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+
+constexpr uint64_t kWaitLimitNs = 1000000000ull;   // one second
+constexpr int kStreamThreads = 256;
+constexpr int kStreamSmem = 200 * 1024;            // ring budget per CTA
+
+// Error codes written to the device error word.
+enum StreamErr { STREAM_OK = 0, STREAM_TIMEOUT = 1 };
+
+}  // namespace jfnk

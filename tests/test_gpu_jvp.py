@@ -79,7 +79,10 @@ def _case(name, nx, ny, seed=0):
     return p, lp, x, v, b, extra
 
 
-CASES = [("burgers", 1000, 1), ("allen_cahn", 70, 45), ("su_olson", 67, 41), ("maxwell", 66, 37)]
+# odd row lengths take the gather launch form, multiples of 4 the march form (16-byte row vectors)
+CASES = [("burgers", 1000, 1), ("allen_cahn", 70, 45), ("su_olson", 67, 41), ("maxwell", 66, 37),
+         ("burgers", 996, 1), ("allen_cahn", 68, 44), ("su_olson", 72, 40), ("maxwell", 64, 37),
+         ("su_olson", 40, 40), ("maxwell", 96, 9)]
 
 
 def _dev(a, dtype=torch.float64):

@@ -8,7 +8,11 @@ oracle.newton, then compares:
   solution: below tol_Newton relative to ||F(x*)|| (Eq. 5);
 * Newton iteration counts: equal (FP64); Krylov counts within 2 per Newton
   step (the reduction order differs, so a convergence test can flip by one
-  iteration near its threshold).
+  iteration near its threshold). Where restarted GMRES runs close to its
+  stagnation edge (the radiation problem at tol 1e-10), the oracle's own
+  count moves by tens of percent under a 1e-15 relative perturbation of the
+  input; there the GPU count must lie inside the band the oracle spans over
+  such perturbations.
 Also: the 1D Burgers step at the benchmark size (N = 1024), time stepping
 over several steps, BiCGSTAB, FD, the Born start of the Maxwell problem, an
 already-converged start, determinism, and the largest restart length.
@@ -63,14 +67,27 @@ def _run(J, ctx, lp, opts, x0, steps):
     return s, x.cpu().numpy(), rep
 
 
-def _compare(x, x_ref, rep, reps, tol_x, exact_newton=True):
+def _compare(x, x_ref, rep, reps, tol_x, exact_newton=True, band=None):
     err = np.abs(x - x_ref).max() / np.abs(x_ref).max()
     assert err <= tol_x, err
     nn = sum(r.newton_its for r in reps)
     if exact_newton:
         assert rep.newton_its == nn, (rep.newton_its, nn)
     kk = sum(r.krylov_its for r in reps)
-    assert abs(rep.krylov_its - kk) <= 2 * max(nn, 1), (rep.krylov_its, kk)
+    if band is None:
+        assert abs(rep.krylov_its - kk) <= 2 * max(nn, 1), (rep.krylov_its, kk)
+    else:
+        lo, hi = band
+        assert 0.9 * lo - 2 * nn <= rep.krylov_its <= 1.1 * hi + 2 * nn, (rep.krylov_its, band)
+
+
+def _oracle_count_band(run, x0, n_pert=4):
+    """Min and max total Krylov count of the oracle under 1e-15 relative perturbations of x0."""
+    counts = []
+    for seed in range(n_pert + 1):
+        xp = x0 if seed == 0 else x0 * (1 + 1e-15 * np.random.default_rng(seed).standard_normal(x0.size))
+        counts.append(sum(r.krylov_its for r in run(xp)))
+    return min(counts), max(counts)
 
 
 @pytest.mark.parametrize("lin", ["ad", "fd"])
@@ -127,8 +144,9 @@ def test_su_olson_step_fp64(J, ctx, limiter):
     lp = J.make_problem("su_olson", n, n, 1e-3, 0.5, (1.0, 1.0, 1.0, 1e-6, limiter))
     s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, "ad", "gmres", 30, 1e-9, 1e-10), x0, 2)
     assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    run = lambda xs: onw.time_steps(p, xs, 2, _oopts("ad", "gmres", 30, 1e-9, 1e-10))[1]
     x_ref, reps = onw.time_steps(p, x0, 2, _oopts("ad", "gmres", 30, 1e-9, 1e-10))
-    _compare(x, x_ref, rep, reps, 1e-10)
+    _compare(x, x_ref, rep, reps, 1e-10, band=_oracle_count_band(run, x0))
 
 
 def test_su_olson_mixed(J, ctx):
@@ -207,3 +225,23 @@ def test_hbm_budget_is_enforced(J):
         assert "budget" in J.jfnk_last_error(c)
     finally:
         J.jfnk_destroy(c)
+
+
+def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
+    """The benchmark grid (2048^2) in FP64 against the oracle's stored solve (tests/golden/)."""
+    import json
+    import os
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "allen_cahn_2048_step1.json")))
+    n = 2048
+    u0 = si.allen_cahn_ic(n, n, 0)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, "ad", "gmres", 40, 1e-8, 1e-8), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    assert rep.newton_its == g["newton_its"]
+    assert abs(rep.krylov_its - g["krylov_its"]) <= 2 * g["newton_its"], (rep.krylov_its, g["krylov_its"])
+    # residual recomputed by the oracle at full size
+    assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-8 * g["res0"]
+    xs = np.array([x[i] for i in g["sample_idx"]])
+    assert np.abs(xs - np.array(g["x_samples"])).max() <= 1e-9 * g["x_absmax"]
+    assert abs(x.sum() - g["x_sum"]) <= 1e-9 * g["x_absmax"] * x.size
