@@ -177,6 +177,40 @@ int jfnk_kernel_stats(jfnk_ctx* ctx, const char** names, long long* launches,
                       double* total_ms, double* bytes, int cap);
 void jfnk_reset_stats(jfnk_ctx* ctx);
 
+/* FD Jacobian-vector product for callers that cannot allocate device memory.
+ * The paper has no counterpart: this is a deployment convenience. Some
+ * callers cannot call cudaMalloc -- code whose device memory belongs to
+ * another allocator or pool, or hot paths that must never reach the driver's
+ * allocator -- and jfnk_jvp needs a context whose workspace is allocated.
+ * This entry point needs no context and allocates nothing: it computes
+ * F(x) and (F(x + eps v) - F(x)) / eps like jfnk_jvp with lin = JFNK_FD,
+ * taking its workspace (the two norms of the step rule and, when F_out is
+ * NULL, F(x)) from one fixed device array that the library holds on every
+ * GPU it is loaded on, until the process exits
+ * (JFNK_NOALLOC_SCRATCH_BYTES).
+ *   prob      host struct as for jfnk_set_problem; for the Maxwell problem
+ *             aux[0] (eps_r) and aux[1] (source) are FP64 device pointers
+ *             (or NULL) used in place, and prec must be JFNK_FP64.
+ *   prec      JFNK_FP64 (double arrays) or JFNK_FP32 (float arrays).
+ *   x, v, b   device arrays of N = nf * nx * ny entries (b may be NULL).
+ *   F_out     device array for F(x), or NULL to keep F(x) in the scratch;
+ *             with NULL, N * sizeof(element) must not exceed
+ *             JFNK_NOALLOC_MAX_FX_BYTES, else JFNK_E_OOM and nothing runs.
+ *   Jv_out    device array for the quotient.
+ *   fd_eps    > 0: the step; otherwise sqrt(eps_mach)(1 + ||x||)/||v||.
+ *   cuda_stream  stream for all work (NULL: the legacy default stream).
+ * Errors: JFNK_E_INVALID for bad arguments, JFNK_E_OOM as above,
+ * JFNK_E_CUDA when a launch fails. Stream-ordered; returns once queued.
+ * The first call on each device looks the scratch array's address up for
+ * that device (with it current); make that first call before capturing the
+ * stream. Every call reuses the same array and clears the part that must
+ * start at zero, so calls that overlap on the GPU (other streams, other host
+ * threads) race on it: serialise them. */
+#define JFNK_NOALLOC_MAX_FX_BYTES 4194304u
+#define JFNK_NOALLOC_SCRATCH_BYTES (4352u + JFNK_NOALLOC_MAX_FX_BYTES)
+jfnk_status jfnk_jvp_fd_noalloc(const jfnk_problem* prob, int prec, const void* x, const void* v, const void* b,
+                                void* F_out, void* Jv_out, double fd_eps, void* cuda_stream);
+
 const char* jfnk_last_error(const jfnk_ctx* ctx);
 const char* jfnk_status_string(int status);
 void jfnk_destroy(jfnk_ctx* ctx);

@@ -32,7 +32,7 @@ JFNK_MAX_RESTART = 64
 
 EXPORTED = ["jfnk_default_opts", "jfnk_create", "jfnk_set_problem", "jfnk_jvp", "jfnk_residual", "jfnk_solve",
             "jfnk_submit", "jfnk_poll", "jfnk_set_timing", "jfnk_kernel_stats", "jfnk_reset_stats",
-            "jfnk_last_error", "jfnk_status_string", "jfnk_destroy"]
+            "jfnk_last_error", "jfnk_status_string", "jfnk_destroy", "jfnk_jvp_fd_noalloc"]
 
 
 class jfnk_problem(C.Structure):
@@ -75,6 +75,7 @@ _sigs = {
     "jfnk_last_error": (C.c_char_p, [_P]),
     "jfnk_status_string": (C.c_char_p, [C.c_int]),
     "jfnk_destroy": (None, [_P]),
+    "jfnk_jvp_fd_noalloc": (C.c_int, [C.POINTER(jfnk_problem), C.c_int, _P, _P, _P, _P, _P, C.c_double, _P]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -172,6 +173,13 @@ def jfnk_status_string(s: int) -> str:
 
 def jfnk_destroy(ctx: int) -> None:
     lib.jfnk_destroy(ctx)
+
+
+def jfnk_jvp_fd_noalloc(prob: jfnk_problem, prec: int, x, v, b, F_out, Jv_out, fd_eps: float = 0.0,
+                        stream: int | None = None) -> int:
+    """FD Jacobian-vector product without a context and without allocating (see include/jfnk.h)."""
+    return lib.jfnk_jvp_fd_noalloc(C.byref(prob), prec, _ptr(x), _ptr(v), _ptr(b), _ptr(F_out), _ptr(Jv_out),
+                                   fd_eps, stream)
 
 
 # --- small conveniences over the same calls ------------------------------------------------------
