@@ -28,6 +28,8 @@ import argparse
 import hashlib
 import json
 import math
+
+import numpy as np
 import os
 import subprocess
 import sys
@@ -59,6 +61,8 @@ def _args():
     ap.add_argument("--cpu-sample-iters", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
+    ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
+    ap.add_argument("--serve-requests", type=int, default=24)
     return ap.parse_args()
 
 
@@ -168,6 +172,81 @@ def _src_hash() -> str:
     for f in sorted(os.listdir(csrc)):
         h.update(open(os.path.join(csrc, f), "rb").read())
     return h.hexdigest()[:16]
+
+
+def served_stream(J, device: int, n_req: int) -> dict:
+    """A bounded request stream through jfnk_submit / jfnk_poll, against the same requests one by one in FP64.
+
+    Requests follow synthetic_inputs.serving_requests (Poisson arrivals at 40/s, log-uniform grids), scaled
+    down to fit a benchmark run: grids 64..512, 1..4 implicit steps, Allen-Cahn and the radiation problem
+    (the Maxwell problem at ten points per wavelength needs the preconditioner the paper uses to converge).
+    Served requests use their drawn precision (mixed FP32 or FP64); the comparison solves every request in
+    plain FP64, one at a time.
+    """
+    import synthetic_inputs as si
+    reqs = [r for r in si.serving_requests(4 * n_req, rate=40.0, seed=7, n_lo=64, n_hi=512, steps_hi=4)
+            if r["pde"] != "maxwell"][:n_req]
+
+    def build(r, prec):
+        n = r["n"]
+        if r["pde"] == "allen_cahn":
+            p = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+            x0 = si.allen_cahn_ic(n, n, r["seed"] % 1000)
+        else:
+            p = J.make_problem("su_olson", n, n, 1e-3, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
+            x0 = si.su_olson_ic(n, n)
+        o = J.jfnk_default_opts(prec)
+        o.restart, o.tol_newton = 40, 1e-8
+        o.tol_krylov = 1e-6 if prec == J.JFNK_MIXED_FP32 else 1e-8
+        return p, o, x0
+
+    ctx = J.jfnk_create(device)
+    try:
+        outs, tickets, t_sub = [], [], []
+        t0 = time.perf_counter()
+        for r in reqs:
+            while time.perf_counter() - t0 < r["t_arrival"]:
+                time.sleep(0.0005)
+            prec = J.JFNK_MIXED_FP32 if r["precision"] == "mixed" else J.JFNK_FP64
+            p, o, x0 = build(r, prec)
+            xo = np.zeros_like(x0)
+            s, t = J.jfnk_submit(ctx, p, o, x0, xo, r["steps"])
+            if s != J.JFNK_OK:
+                raise RuntimeError("submit: " + J.jfnk_status_string(s))
+            outs.append((xo, x0, p))
+            tickets.append(t)
+        lat, ok = [], 0
+        pending = dict(enumerate(tickets))
+        while pending:
+            for i, t in list(pending.items()):
+                rep = J.jfnk_report()
+                s = J.jfnk_poll(ctx, t, rep)
+                if s != J.JFNK_E_BUSY:
+                    lat.append(rep.ms)
+                    ok += (s == J.JFNK_OK)
+                    del pending[i]
+            time.sleep(0.0005)
+        wall = time.perf_counter() - t0
+    finally:
+        J.jfnk_destroy(ctx)
+    steps = sum(r["steps"] for r in reqs)
+    # the same requests, one at a time, plain FP64
+    c1 = J.jfnk_create(device)
+    try:
+        t1 = time.perf_counter()
+        for r in reqs:
+            p, o, x0 = build(r, J.JFNK_FP64)
+            J.check(c1, J.jfnk_set_problem(c1, p), "set_problem")
+            xa = x0.copy()
+            J.jfnk_solve(c1, o, None, xa, r["steps"], None)
+        one = time.perf_counter() - t1
+    finally:
+        J.jfnk_destroy(c1)
+    lat.sort()
+    return {"requests": len(reqs), "solves": steps, "completed": ok, "value": steps / wall, "unit": "solves/s",
+            "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "fp64_one_by_one": {"value": steps / one, "unit": "solves/s"},
+            "stream": "Poisson 40/s, Allen-Cahn + radiation, grids 64..512, 1..4 steps, precision mixed|fp64"}
 
 
 def run_reference(a) -> None:
@@ -338,6 +417,7 @@ def main() -> None:
 
     cpu = cpu_baseline(a.cpu_sample_iters) if (rank == 0 and world == 1 and not a.no_cpu) else None
     J.jfnk_destroy(ctx)
+    served = None if a.no_serve else served_stream(J, local, a.serve_requests)
     if rank != 0:
         return
     out = {
@@ -354,7 +434,7 @@ def main() -> None:
         "jvp_gbs": jvp_gbs, "jvp_frac": (jvp_gbs / peak) if jvp_gbs else None,
         "fp64_plain": fp64, "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches,
         "timed_with_kernel_events_ms_per_step": sum(ms_t) / a.steps,
-        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk,
+        "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "served": served,
     }
     print(json.dumps(out))
 

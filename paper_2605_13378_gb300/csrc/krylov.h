@@ -28,6 +28,12 @@ cudaError_t launch_gmres_finish(int tb, int td, long long n, const void* V, void
 // 3 update + norm + Givens (Arnoldi step k - 1), 4 solution update d += V y
 // over ctl->k vectors (kmax an upper bound known to the host). nsm CTAs.
 bool stream_supported(long long n);
+cudaError_t basis_stream_f64(int mode, long long n, const void* V, int k, int kmax, void* w, void* d, GmresCtl* ctl,
+                             RedWs red, unsigned int* err, int nsm, cudaStream_t st);
+cudaError_t basis_stream_f32(int mode, int td, long long n, const void* V, int k, int kmax, void* w, void* d,
+                             GmresCtl* ctl, RedWs red, unsigned int* err, int nsm, cudaStream_t st);
+cudaError_t basis_stream_bf16(int mode, long long n, const void* V, int k, int kmax, void* w, void* d,
+                              GmresCtl* ctl, RedWs red, unsigned int* err, int nsm, cudaStream_t st);
 cudaError_t launch_basis_stream(int mode, int tb, int tj, int td, long long n, const void* V, int k, int kmax,
                                 void* w, void* d, GmresCtl* ctl, RedWs red, unsigned int* err, int nsm,
                                 cudaStream_t st);

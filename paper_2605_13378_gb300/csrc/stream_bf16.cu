@@ -1,0 +1,12 @@
+// stream_bf16.cu -- the basis streaming kernel for the BF16 basis
+// (see stream_impl.cuh), in a translation unit of its own.
+#include "stream_impl.cuh"
+
+namespace jfnk {
+
+cudaError_t basis_stream_bf16(int mode, long long n, const void* V, int k, int kmax, void* w, void* d,
+                              GmresCtl* ctl, RedWs red, unsigned int* err, int nsm, cudaStream_t st) {
+  return stream_mode<__nv_bfloat16, float, double>(mode, n, V, k, kmax, w, d, ctl, red, err, nsm, st);
+}
+
+}  // namespace jfnk
