@@ -380,7 +380,9 @@ def main() -> None:
     if os.path.exists(TRAFFIC):
         tr = json.load(open(TRAFFIC))
         if tr.get("src_hash") == _src_hash() and dom in tr.get("kernels", {}):
-            traffic = tr["kernels"][dom]["dram_bytes_per_launch"]
+            # ncu's DRAM bytes over the algorithmic bytes of the captured launches, scaled to this
+            # class's mean algorithmic bytes per launch (launches differ in basis size k)
+            traffic = round(tr["kernels"][dom]["dram_over_algorithmic"] * stats[dom]["bytes"] / stats[dom]["launches"])
     roofline = {"bound": "hbm", "kernel": dom, "achieved": ach, "peak": peak, "unit": "GB/s",
                 "frac": round(ach / peak, 4) if ach else None, "traffic": traffic,
                 "peak_source": "measured" if peaks else "fallback",
