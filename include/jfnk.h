@@ -154,6 +154,39 @@ jfnk_status jfnk_residual(jfnk_ctx* ctx, int prec, const void* x, const void* b,
 jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_prev,
                        double* x_inout, int steps, jfnk_report* rep);
 
+/* Batched solves: `count` independent problems solved together, each with
+ * its own options (probs[i], opts[i]) and step count (steps[i]; ignored for
+ * the Maxwell problem), each exactly as jfnk_solve would define it (Newton
+ * with the Armijo line search of Sec. 2, restarted GMRES with CGS2 Arnoldi
+ * of Sec. 3, the AD JVP of Eq. 9 or the FD quotient of Eq. 7, the theta
+ * method of Eq. 2, the Born start). The state of every solve lives on the
+ * device; each launch of the batch kernel advances every unfinished solve by
+ * one phase of that iteration (a JVP sweep, one Gram-Schmidt pass, a
+ * residual, a line-search trial ...), and the host replays a captured CUDA
+ * graph of such launches until all are done, so small solves share launches
+ * instead of each paying its own launch and synchronisation latency.
+ * Supported: krylov = JFNK_GMRES, prec = JFNK_FP64, JFNK_FP32 or
+ * JFNK_MIXED_FP32 (JFNK_E_INVALID otherwise, nothing runs). The problems do
+ * not use the context's installed problem. x_prev[i] (x_prev or x_prev[i]
+ * may be NULL: start from x_inout[i]) and x_inout[i] are FP64 host or device
+ * arrays of the problem's size; results are written to x_inout[i].
+ * Reductions are summed in a fixed order over 256-cell units of each
+ * problem, so a problem's result does not depend on the other problems of
+ * the batch, on the tile size or on the grid (it differs from jfnk_solve's
+ * at rounding level). reps[i] (may be NULL) gets each solve's counts,
+ * statuses[i] (may be NULL) its status as jfnk_solve would return it.
+ * Synchronous. Returns the first non-OK status in index order, JFNK_E_OOM
+ * when the summed workspace exceeds the context's HBM budget. */
+jfnk_status jfnk_solve_batch(jfnk_ctx* ctx, int count, const jfnk_problem* probs, const jfnk_opts* opts,
+                             const double* const* x_prev, double* const* x_inout, const int* steps,
+                             jfnk_report* reps, int* statuses);
+
+/* Batch engine counters: kernel launches issued by jfnk_solve_batch (and the
+ * batched part of the server) so far, and the tile size (cells) the
+ * autotuner chose for problems of this PDE, precision and grid (0: none yet). */
+jfnk_status jfnk_batch_stats(jfnk_ctx* ctx, long long* kernel_launches, int* tile_cells, int pde, int prec,
+                             int nx, int ny);
+
 /* Serving: queue a solve of `prob` (steps as in jfnk_solve) and return a
  * ticket at once. x0 and x_out are FP64 host or device arrays that must stay
  * valid until jfnk_poll returns a final status for the ticket. Requests are

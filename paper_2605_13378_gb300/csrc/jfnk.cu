@@ -11,6 +11,7 @@
 // stops issuing steps when it sees the flag, at most kLookahead steps late.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <chrono>
 #include <cmath>
 #include <cstdio>
@@ -19,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "batch_engine.h"
 #include "jfnk.h"
 #include "kernels.h"
 #include "krylov.h"
@@ -110,6 +112,7 @@ struct jfnk_ctx {
   size_t jscratch_bytes = 0;
   Timer tm;
   jfnk::Server* server = nullptr;
+  jfnk::BatchEngine* batch = nullptr;   // jfnk_solve_batch
 };
 
 namespace {
@@ -650,6 +653,7 @@ jfnk_status jfnk_create(jfnk_ctx** out, int device, size_t hbm_budget, void* cud
 void jfnk_destroy(jfnk_ctx* ctx) {
   if (!ctx) return;
   if (ctx->server) { delete ctx->server; ctx->server = nullptr; }
+  if (ctx->batch) { delete ctx->batch; ctx->batch = nullptr; }
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ws_free(ctx);
@@ -670,49 +674,11 @@ const char* jfnk_last_error(const jfnk_ctx* ctx) { return ctx ? ctx->err.c_str()
 jfnk_status jfnk_set_problem(jfnk_ctx* ctx, const jfnk_problem* pr) {
   if (!ctx || !pr) return JFNK_E_INVALID;
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  const int pde = pr->pde;
-  if (pde < 0 || pde > 3) return fail(ctx, JFNK_E_INVALID, "unknown pde");
-  if (pde == JFNK_BURGERS1D) {
-    if (pr->ny != 1 || pr->nx < 3) return fail(ctx, JFNK_E_INVALID, "burgers1d needs nx >= 3 and ny == 1");
-  } else if (pr->nx < 3 || pr->ny < 3) {
-    return fail(ctx, JFNK_E_INVALID, "2D problems need nx, ny >= 3");
-  }
-  if ((long long)pr->nx * pr->ny > (1LL << 30)) return fail(ctx, JFNK_E_INVALID, "grid too large");
-  const bool bvp = (pde == JFNK_MAXWELL_TE2D);
-  if (!bvp && !(pr->dt > 0.0 && pr->theta >= 0.0 && pr->theta <= 1.0 && std::isfinite(pr->dt)))
-    return fail(ctx, JFNK_E_INVALID, "time step needs dt > 0 and 0 <= theta <= 1");
-  if (pde == JFNK_SU_OLSON2D && !(pr->p[0] > 0.0 && pr->p[1] > 0.0))
-    return fail(ctx, JFNK_E_INVALID, "su_olson needs sigma > 0 and a > 0");
-  if (pde == JFNK_MAXWELL_TE2D && !(pr->p[0] > 0.0)) return fail(ctx, JFNK_E_INVALID, "maxwell needs k > 0");
-  cudaStreamSynchronize(ctx->stream);
   ProbDev P;
-  std::memset(&P, 0, sizeof(P));
-  P.pde = pde;
-  P.nx = pr->nx;
-  P.ny = pr->ny;
-  P.nf = (pde == JFNK_SU_OLSON2D || pde == JFNK_MAXWELL_TE2D) ? 2 : 1;
-  P.ncell = (long long)pr->nx * pr->ny;
-  P.bvp = bvp ? 1 : 0;
-  P.thdt = bvp ? 1.0 : pr->theta * pr->dt;
-  P.c_old = bvp ? 0.0 : (1.0 - pr->theta) * pr->dt;
-  P.invhx = (double)pr->nx;
-  P.invhy = (double)pr->ny;
-  P.invhx2 = (double)pr->nx * (double)pr->nx;
-  P.invhy2 = (double)pr->ny * (double)pr->ny;
-  P.p0 = pr->p[0]; P.p1 = pr->p[1]; P.p2 = pr->p[2]; P.p3 = pr->p[3];
-  if (pde == JFNK_SU_OLSON2D) {
-    P.flag = pr->p[4] != 0.0;
-    const double Db = 1.0 / (3.0 * pr->p[0]);
-    const double Finc = 0.25 * pr->p[1] * std::pow(pr->p[2], 4.0);
-    const double hx = 1.0 / pr->nx;
-    P.mq_b = 2.0 * Db / (hx + 4.0 * Db);
-    P.mq_a = P.mq_b * 4.0 * Finc;
-  }
-  if (pde == JFNK_MAXWELL_TE2D) {
-    const double ax = 0.5 * pr->p[0] / pr->nx, ay = 0.5 * pr->p[0] / pr->ny;
-    P.cxr = (1.0 - ax * ax) / (1.0 + ax * ax); P.cxi = 2.0 * ax / (1.0 + ax * ax);
-    P.cyr = (1.0 - ay * ay) / (1.0 + ay * ay); P.cyi = 2.0 * ay / (1.0 + ay * ay);
-  }
+  std::string why;
+  if (!make_probdev(pr, &P, &why)) return fail(ctx, JFNK_E_INVALID, why);
+  const int pde = pr->pde;
+  cudaStreamSynchronize(ctx->stream);
   // problem-owned arrays
   cudaFree(ctx->eps64); cudaFree(ctx->eps32); cudaFree(ctx->src64); cudaFree(ctx->src32);
   ctx->eps64 = nullptr; ctx->eps32 = nullptr; ctx->src64 = nullptr; ctx->src32 = nullptr;
@@ -955,6 +921,90 @@ jfnk_status jfnk_submit(jfnk_ctx* ctx, const jfnk_problem* prob, const jfnk_opts
   if (!ctx || !prob || !opts || !x0 || !x_out || !ticket) return JFNK_E_INVALID;
   if (!ctx->server) ctx->server = new jfnk::Server(ctx->device, ctx->budget, 4);
   return ctx->server->submit(prob, opts, x0, x_out, steps, ticket);
+}
+
+jfnk_status jfnk_solve_batch(jfnk_ctx* ctx, int count, const jfnk_problem* probs, const jfnk_opts* opts,
+                             const double* const* x_prev, double* const* x_inout, const int* steps,
+                             jfnk_report* reps, int* statuses) {
+  if (!ctx || count < 0) return JFNK_E_INVALID;
+  if (count == 0) return JFNK_OK;
+  if (!probs || !opts || !x_inout || !steps) return fail(ctx, JFNK_E_INVALID, "null array");
+  size_t need = 0;
+  for (int i = 0; i < count; ++i) {
+    std::string why;
+    if (!jfnk::BatchEngine::supports(&probs[i], &opts[i], &why))
+      return fail(ctx, JFNK_E_INVALID, "problem " + std::to_string(i) + ": " + why);
+    if (!x_inout[i]) return fail(ctx, JFNK_E_INVALID, "problem " + std::to_string(i) + ": null state");
+    if (probs[i].pde != JFNK_MAXWELL_TE2D && steps[i] < 1)
+      return fail(ctx, JFNK_E_INVALID, "problem " + std::to_string(i) + ": steps must be >= 1");
+    need += jfnk::BatchEngine::workspace_bytes(&probs[i], &opts[i]);
+  }
+  if (ctx->budget && ctx->allocated + need > ctx->budget)
+    return fail(ctx, JFNK_E_OOM, "batch workspace of " + std::to_string(need) + " bytes exceeds the HBM budget");
+  CK(cudaSetDevice(ctx->device), "cudaSetDevice");
+  CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");   // caller's inputs are ready
+  if (!ctx->batch) ctx->batch = new jfnk::BatchEngine(ctx->device);
+  jfnk::BatchEngine& E = *ctx->batch;
+  std::string why;
+  for (int i = 0; i < count; ++i) {
+    jfnk::BatRequest r;
+    r.prob = probs[i];
+    r.opts = opts[i];
+    r.x0 = (x_prev && x_prev[i]) ? x_prev[i] : x_inout[i];
+    r.x_out = x_inout[i];
+    r.steps = steps[i];
+    r.tag = (unsigned long long)i;
+    jfnk_status s = E.admit(r, &why);
+    if (s) {
+      E.drop_all();
+      return fail(ctx, s, "admit " + std::to_string(i) + ": " + why);
+    }
+  }
+  // every solve ends after a bounded number of phases: stop replaying past that bound
+  long long bound = 0;
+  for (int i = 0; i < count; ++i) {
+    const jfnk_opts& o = opts[i];
+    const long long per_newton = (long long)o.max_krylov * (4LL * o.restart + 3) + 16;
+    const long long solves = (probs[i].pde == JFNK_MAXWELL_TE2D) ? 2 : steps[i];
+    bound = std::max(bound, solves * (o.max_newton + 1) * per_newton + 8);
+  }
+  std::vector<jfnk_status> st(count, JFNK_OK);
+  std::vector<jfnk::BatResult> fin;
+  long long phases = 0;
+  while (E.active() > 0) {
+    if (phases > bound) {
+      E.drop_all();
+      return fail(ctx, JFNK_E_TIMEOUT, "batch: a solve did not finish within its phase bound");
+    }
+    phases += E.launches_per_replay();
+    fin.clear();
+    jfnk_status s = E.advance(&fin, &why);
+    if (s) {
+      E.drop_all();
+      return fail(ctx, s, "batch: " + why);
+    }
+    for (const jfnk::BatResult& r : fin) {
+      st[r.tag] = r.status;
+      if (reps) reps[r.tag] = r.rep;
+    }
+  }
+  jfnk_status first = JFNK_OK;
+  for (int i = 0; i < count; ++i) {
+    if (statuses) statuses[i] = st[i];
+    if (first == JFNK_OK && st[i] != JFNK_OK) first = st[i];
+  }
+  return first;
+}
+
+jfnk_status jfnk_batch_stats(jfnk_ctx* ctx, long long* kernel_launches, int* tile_cells, int pde, int prec,
+                             int nx, int ny) {
+  if (!ctx) return JFNK_E_INVALID;
+  if (kernel_launches) *kernel_launches = ctx->batch ? ctx->batch->kernel_launches() : 0;
+  if (tile_cells) {
+    *tile_cells = 0;
+    if (ctx->batch) *tile_cells = ctx->batch->tuned_tile(pde, prec, (long long)nx * ny);
+  }
+  return JFNK_OK;
 }
 
 jfnk_status jfnk_poll(jfnk_ctx* ctx, unsigned long long ticket, jfnk_report* rep) {

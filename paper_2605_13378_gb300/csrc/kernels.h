@@ -6,6 +6,10 @@
 #include <cuda_runtime.h>
 #include <stddef.h>
 
+#include <string>
+
+#include "jfnk.h"
+
 #include "pdes.cuh"
 
 namespace jfnk {
@@ -35,6 +39,10 @@ struct StencilGeom {
   int max_blocks;          // largest grid of any stencil launch form of the problem (reduction capacity)
 };
 StencilGeom stencil_geom(const ProbDev& P);
+
+// Validate a problem and derive the kernels' constants (aux pointers left
+// null); on failure *why (may be null) says what is wrong.
+bool make_probdev(const jfnk_problem* pr, ProbDev* P, std::string* why);
 
 // F = F(x + alpha d; b) in precision t (x, d, b, F, xout of type t; d, b,
 // F, xout, x32 may be null). sums[0] = ||F||^2, sums[1] = ||x + alpha d||^2

@@ -108,40 +108,8 @@ __global__ void __launch_bounds__(256) k_na_norms(long long n, const T* __restri
 // Derived constants of a problem, as jfnk_set_problem computes them; the aux
 // arrays are used in place (FP64 device pointers).
 static bool na_problem(const jfnk_problem* pr, ProbDev* P) {
-  const int pde = pr->pde;
-  if (pde < 0 || pde > 3) return false;
-  if (pde == JFNK_BURGERS1D ? (pr->ny != 1 || pr->nx < 3) : (pr->nx < 3 || pr->ny < 3)) return false;
-  if ((long long)pr->nx * pr->ny > (1LL << 30)) return false;
-  const bool bvp = (pde == JFNK_MAXWELL_TE2D);
-  if (!bvp && !(pr->dt > 0.0 && pr->theta >= 0.0 && pr->theta <= 1.0)) return false;
-  if (pde == JFNK_SU_OLSON2D && !(pr->p[0] > 0.0 && pr->p[1] > 0.0)) return false;
-  if (pde == JFNK_MAXWELL_TE2D && !(pr->p[0] > 0.0)) return false;
-  memset(P, 0, sizeof(*P));
-  P->pde = pde;
-  P->nx = pr->nx;
-  P->ny = pr->ny;
-  P->nf = (pde == JFNK_SU_OLSON2D || pde == JFNK_MAXWELL_TE2D) ? 2 : 1;
-  P->ncell = (long long)pr->nx * pr->ny;
-  P->bvp = bvp ? 1 : 0;
-  P->thdt = bvp ? 1.0 : pr->theta * pr->dt;
-  P->c_old = bvp ? 0.0 : (1.0 - pr->theta) * pr->dt;
-  P->invhx = (double)pr->nx;
-  P->invhy = (double)pr->ny;
-  P->invhx2 = (double)pr->nx * (double)pr->nx;
-  P->invhy2 = (double)pr->ny * (double)pr->ny;
-  P->p0 = pr->p[0]; P->p1 = pr->p[1]; P->p2 = pr->p[2]; P->p3 = pr->p[3];
-  if (pde == JFNK_SU_OLSON2D) {
-    P->flag = pr->p[4] != 0.0;
-    const double Db = 1.0 / (3.0 * pr->p[0]);
-    const double Finc = 0.25 * pr->p[1] * pow(pr->p[2], 4.0);
-    const double hx = 1.0 / pr->nx;
-    P->mq_b = 2.0 * Db / (hx + 4.0 * Db);
-    P->mq_a = P->mq_b * 4.0 * Finc;
-  }
-  if (pde == JFNK_MAXWELL_TE2D) {
-    const double ax = 0.5 * pr->p[0] / pr->nx, ay = 0.5 * pr->p[0] / pr->ny;
-    P->cxr = (1.0 - ax * ax) / (1.0 + ax * ax); P->cxi = 2.0 * ax / (1.0 + ax * ax);
-    P->cyr = (1.0 - ay * ay) / (1.0 + ay * ay); P->cyi = 2.0 * ay / (1.0 + ay * ay);
+  if (!make_probdev(pr, P, nullptr)) return false;
+  if (pr->pde == JFNK_MAXWELL_TE2D) {
     P->eps64 = pr->aux[0];
     P->src64 = pr->aux[1];
   }

@@ -32,7 +32,8 @@ JFNK_MAX_RESTART = 64
 
 EXPORTED = ["jfnk_default_opts", "jfnk_create", "jfnk_set_problem", "jfnk_jvp", "jfnk_residual", "jfnk_solve",
             "jfnk_submit", "jfnk_poll", "jfnk_set_timing", "jfnk_kernel_stats", "jfnk_reset_stats",
-            "jfnk_last_error", "jfnk_status_string", "jfnk_destroy", "jfnk_jvp_fd_noalloc"]
+            "jfnk_last_error", "jfnk_status_string", "jfnk_destroy", "jfnk_jvp_fd_noalloc", "jfnk_solve_batch",
+            "jfnk_batch_stats"]
 
 
 class jfnk_problem(C.Structure):
@@ -76,6 +77,10 @@ _sigs = {
     "jfnk_status_string": (C.c_char_p, [C.c_int]),
     "jfnk_destroy": (None, [_P]),
     "jfnk_jvp_fd_noalloc": (C.c_int, [C.POINTER(jfnk_problem), C.c_int, _P, _P, _P, _P, _P, C.c_double, _P]),
+    "jfnk_solve_batch": (C.c_int, [_P, C.c_int, C.POINTER(jfnk_problem), C.POINTER(jfnk_opts), _P, _P,
+                                   C.POINTER(C.c_int), C.POINTER(jfnk_report), C.POINTER(C.c_int)]),
+    "jfnk_batch_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
+                                   C.c_int]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -180,6 +185,36 @@ def jfnk_jvp_fd_noalloc(prob: jfnk_problem, prec: int, x, v, b, F_out, Jv_out, f
     """FD Jacobian-vector product without a context and without allocating (see include/jfnk.h)."""
     return lib.jfnk_jvp_fd_noalloc(C.byref(prob), prec, _ptr(x), _ptr(v), _ptr(b), _ptr(F_out), _ptr(Jv_out),
                                    fd_eps, stream)
+
+
+def jfnk_solve_batch(ctx: int, probs, opts, x_prev, x_inout, steps) -> tuple[int, list, list]:
+    """Solve len(probs) problems together; opts and steps may be one value for all.
+
+    Returns (status, reports, statuses). x_prev may be None or contain None entries.
+    """
+    n = len(probs)
+    if isinstance(opts, jfnk_opts):
+        opts = [opts] * n
+    if isinstance(steps, int):
+        steps = [steps] * n
+    P = (jfnk_problem * n)(*probs)
+    O = (jfnk_opts * n)(*opts)
+    xp = None if x_prev is None else (C.c_void_p * n)(*[_ptr(a) for a in x_prev])
+    xi = (C.c_void_p * n)(*[_ptr(a) for a in x_inout])
+    st = (C.c_int * n)(*steps)
+    R = (jfnk_report * n)()
+    S = (C.c_int * n)()
+    s = lib.jfnk_solve_batch(ctx, n, P, O, C.cast(xp, C.c_void_p) if xp is not None else None,
+                             C.cast(xi, C.c_void_p), st, R, S)
+    return s, [R[i] for i in range(n)], [S[i] for i in range(n)]
+
+
+def jfnk_batch_stats(ctx: int, pde: int = 0, prec: int = 0, nx: int = 0, ny: int = 0) -> tuple[int, int]:
+    """(kernel launches of the batch engine so far, tuned tile cells for that problem class or 0)."""
+    kl = C.c_longlong()
+    tc = C.c_int()
+    lib.jfnk_batch_stats(ctx, C.byref(kl), C.byref(tc), pde, prec, nx, ny)
+    return kl.value, tc.value
 
 
 # --- small conveniences over the same calls ------------------------------------------------------
