@@ -232,6 +232,7 @@ def served_stream(J, device: int, n_req: int) -> dict:
     steps = sum(r["steps"] for r in reqs)
     # the same requests, one at a time, plain FP64
     c1 = J.jfnk_create(device)
+    x64 = []
     try:
         t1 = time.perf_counter()
         for r in reqs:
@@ -239,13 +240,34 @@ def served_stream(J, device: int, n_req: int) -> dict:
             J.check(c1, J.jfnk_set_problem(c1, p), "set_problem")
             xa = x0.copy()
             J.jfnk_solve(c1, o, None, xa, r["steps"], None)
+            x64.append(xa)
         one = time.perf_counter() - t1
     finally:
         J.jfnk_destroy(c1)
+    # the same requests in their drawn precision, all in one jfnk_solve_batch call (second of two calls:
+    # the first includes the tile autotuner's probes)
+    cb = J.jfnk_create(device)
+    try:
+        for rep_i in range(2):
+            built = [build(r, J.JFNK_MIXED_FP32 if r["precision"] == "mixed" else J.JFNK_FP64) for r in reqs]
+            xb = [b[2].copy() for b in built]
+            l0 = J.jfnk_batch_stats(cb)[0]
+            tb = time.perf_counter()
+            sb, _, sts = J.jfnk_solve_batch(cb, [b[0] for b in built], [b[1] for b in built], None, xb,
+                                            [r["steps"] for r in reqs])
+            bwall = time.perf_counter() - tb
+            blaunch = J.jfnk_batch_stats(cb)[0] - l0
+    finally:
+        J.jfnk_destroy(cb)
+    rel = lambda a, b: float(np.abs(a - b).max() / np.abs(b).max())
     lat.sort()
     return {"requests": len(reqs), "solves": steps, "completed": ok, "value": steps / wall, "unit": "solves/s",
             "p50_ms": lat[len(lat) // 2], "p99_ms": lat[min(len(lat) - 1, int(math.ceil(0.99 * len(lat))) - 1)],
+            "max_rel_diff_vs_fp64": max(rel(o[0], x) for o, x in zip(outs, x64)),
             "fp64_one_by_one": {"value": steps / one, "unit": "solves/s"},
+            "batched_one_call": {"value": steps / bwall, "unit": "solves/s", "kernel_launches": blaunch,
+                                 "completed": sum(1 for q in sts if q == 0),
+                                 "max_rel_diff_vs_fp64": max(rel(a, x) for a, x in zip(xb, x64))},
             "stream": "Poisson 40/s, Allen-Cahn + radiation, grids 64..512, 1..4 steps, precision mixed|fp64"}
 
 
