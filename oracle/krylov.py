@@ -10,6 +10,11 @@ of Eq. 10 is r0 = b, and stop on the relative residual ||r|| <= tol ||b||
                Hessenberg matrix, least-squares update at the end of a cycle,
                at most ``max_cycles`` restart cycles (the paper's Krylov cap
                counts restart cycles for GMRES, Sec. 3.3).
+* ``gmres_dcgs2`` the same GMRES(m) with the second Gram-Schmidt pass of each
+               Arnoldi vector delayed by one step (delayed CGS2, Swirydowicz et
+               al. 2020; Bielich et al. 2022), so that one set of inner products
+               per step serves both passes. Same Krylov space, basis and
+               iterates as CGS2 in exact arithmetic.
 * ``bicgstab`` van der Vorst's BiCGSTAB with shadow residual r_hat = r0.
 * ``cg``       Hestenes-Stiefel conjugate gradients for SPD systems.
 """
@@ -104,6 +109,113 @@ def gmres(A, b: np.ndarray, m: int, tol: float, max_cycles: int) -> KrylovResult
         for i in range(k - 1, -1, -1):
             y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
         x = x + V[:k].T @ y
+        if not np.all(np.isfinite(x)):
+            return KrylovResult(x, its, mv, False, True, float("nan"))
+        if done:
+            return KrylovResult(x, its, mv, resid <= target, False, resid)
+    return KrylovResult(x, its, mv, False, False, resid)
+
+
+def gmres_dcgs2(A, b: np.ndarray, m: int, tol: float, max_cycles: int) -> KrylovResult:
+    """Restarted GMRES(m) with delayed CGS2 Arnoldi, starting from x = 0.
+
+    Step j holds a candidate u_j that has been projected once against
+    q_0 .. q_{j-1} but neither projected a second time nor normalised; it is
+    scaled to unit length (ut = u_j / ||u_j||) and the operator is applied to
+    it, w = A ut. One set of inner products, s = Q^T ut, alpha = ut.ut,
+    t = Q^T w, beta = ut.w, then gives
+      * the second projection of the candidate: rho^2 = alpha - s.s is the
+        squared norm of ut - Q s, q_j = (ut - Q s) / rho, and column j-1 of
+        the Hessenberg matrix is completed as (first projection + s / sigma,
+        rho / sigma) with sigma = 1 / ||u_j||, rotated and tested for
+        convergence (one step after CGS2 would);
+      * the first projection of A q_j: A q_j = (w - A Q s) / rho with
+        A Q = Q_{j+1} H[:j+1, :j] (the completed columns), so
+        h_i = (t_i - z_i) / rho for i < j and h_j = ((beta - s.t)/rho - z_j)/rho
+        with z = H[:j+1, :j] s;
+      * the next candidate u_{j+1} = A q_j - Q_{j+1} h.
+    The last column of a cycle is completed by the inner products of u_m alone.
+    """
+    n = b.size
+    x = np.zeros(n)
+    bnorm = float(np.linalg.norm(b))
+    its = 0
+    mv = 0
+    if bnorm == 0.0:
+        return KrylovResult(x, 0, 0, True, False, 0.0)
+    target = tol * bnorm
+    resid = bnorm
+    for cycle in range(max_cycles):
+        if cycle == 0:
+            r = b.copy()
+        else:
+            r = b - A(x)
+            mv += 1
+        beta0 = float(np.linalg.norm(r))
+        resid = beta0
+        if beta0 <= target:
+            return KrylovResult(x, its, mv, True, False, beta0)
+        Q = np.zeros((m + 1, n))
+        Hraw = np.zeros((m + 1, m))      # completed columns, before rotation
+        H = np.zeros((m + 1, m))         # the same columns, rotated
+        cs = np.zeros(m)
+        sn = np.zeros(m)
+        g = np.zeros(m + 1)
+        u = r
+        sigma = 1.0 / beta0
+        hprev = None
+        k = 0
+        done = False
+        for j in range(m + 1):
+            ut = sigma * u
+            s = Q[:j] @ ut
+            alpha = float(ut @ ut)
+            if j < m:
+                w = A(ut)
+                mv += 1
+                t = Q[:j] @ w
+                bt = float(ut @ w)
+            rho2 = alpha - float(s @ s)
+            rho = float(np.sqrt(rho2)) if rho2 > 0.0 else 0.0
+            if j == 0:
+                g[0] = beta0 * rho       # r = beta0 * rho * q_0
+            else:
+                # complete column j-1, rotate it, test: A q_{j-1} = Q h + u_j and
+                # u_j = ut / sigma = (Q s + rho q_j) / sigma
+                c_ = j - 1
+                Hraw[:j, c_] = hprev[:j] + s / sigma
+                Hraw[j, c_] = rho / sigma
+                H[: j + 1, c_] = Hraw[: j + 1, c_]
+                for i in range(c_):
+                    tt = cs[i] * H[i, c_] + sn[i] * H[i + 1, c_]
+                    H[i + 1, c_] = -sn[i] * H[i, c_] + cs[i] * H[i + 1, c_]
+                    H[i, c_] = tt
+                cs[c_], sn[c_] = givens(H[c_, c_], H[c_ + 1, c_])
+                H[c_, c_] = cs[c_] * H[c_, c_] + sn[c_] * H[c_ + 1, c_]
+                H[c_ + 1, c_] = 0.0
+                g[c_ + 1] = -sn[c_] * g[c_]
+                g[c_] = cs[c_] * g[c_]
+                its += 1
+                k = j
+                resid = abs(g[c_ + 1])
+                if resid <= target or rho == 0.0:
+                    done = True
+                    break
+                if j == m:
+                    break
+            Q[j] = (ut - Q[:j].T @ s) / rho
+            z = Hraw[: j + 1, :j] @ s
+            h = np.empty(j + 1)
+            h[:j] = (t - z[:j]) / rho
+            h[j] = ((bt - float(s @ t)) / rho - z[j]) / rho
+            hprev = h
+            u = (w - Q[: j + 1].T @ (z + rho * h)) / rho
+            un = float(np.linalg.norm(u))
+            sigma = 1.0 / un if un > 0.0 else 0.0
+        y = np.zeros(k)
+        for i in range(k - 1, -1, -1):
+            y[i] = (g[i] - H[i, i + 1:k] @ y[i + 1:k]) / H[i, i]
+        x = x + Q[:k].T @ y
         if not np.all(np.isfinite(x)):
             return KrylovResult(x, its, mv, False, True, float("nan"))
         if done:

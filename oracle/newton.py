@@ -34,6 +34,7 @@ from . import krylov as _kr
 class Options:
     lin: str = "ad"            # "ad" | "fd"
     krylov: str = "gmres"      # "gmres" | "bicgstab" | "cg"
+    ortho: str = "cgs2"        # GMRES Arnoldi: "cgs2" | "dcgs2" (second pass delayed one step)
     restart: int = 30
     max_cycles: int = 100      # GMRES restart cycles; iteration cap for BiCGSTAB / CG
     max_newton: int = 15
@@ -83,6 +84,8 @@ def _operator(problem, b, x, Fx, opt: Options, rep: Report):
 
 def _krylov(A, rhs, opt: Options):
     if opt.krylov == "gmres":
+        if opt.ortho == "dcgs2":
+            return _kr.gmres_dcgs2(A, rhs, opt.restart, opt.tol_krylov, opt.max_cycles)
         return _kr.gmres(A, rhs, opt.restart, opt.tol_krylov, opt.max_cycles)
     if opt.krylov == "bicgstab":
         return _kr.bicgstab(A, rhs, opt.tol_krylov, opt.max_cycles)

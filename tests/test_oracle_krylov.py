@@ -107,3 +107,84 @@ def test_gmres_on_circulant_allen_cahn_matches_fft():
     lam = 1.0 - th * dt * (D * (sym1[None, :] + sym1[:, None]) + 1.0 - 3.0 * c * c)
     x_fft = np.real(np.fft.ifft2(np.fft.fft2(b.reshape(n, n)) / lam)).reshape(-1)
     assert np.allclose(r.x, x_fft, rtol=1e-9, atol=1e-10 * np.abs(x_fft).max())
+
+
+# ---------------------------------------------------------------------------
+# delayed CGS2 (the second Gram-Schmidt pass one Arnoldi step late)
+# ---------------------------------------------------------------------------
+def test_dcgs2_gmres_full_equals_dense_solve(rng):
+    n = 32
+    A = _nonsym(rng, n, 1.0)
+    b = rng.standard_normal(n)
+    r = krylov.gmres_dcgs2(lambda v: A @ v, b, m=n, tol=1e-14, max_cycles=1)
+    assert r.converged
+    assert np.allclose(r.x, np.linalg.solve(A, b), rtol=1e-9, atol=1e-11)
+
+
+@pytest.mark.parametrize("k", [1, 2, 5, 9])
+def test_dcgs2_gmres_is_minimum_residual_over_krylov_space(rng, k):
+    """After k completed columns the iterate is the minimum-residual point of K_k (lstsq on a power basis)."""
+    n = 24
+    A = _nonsym(rng, n, 0.5)
+    b = rng.standard_normal(n)
+    r = krylov.gmres_dcgs2(lambda v: A @ v, b, m=k, tol=0.0, max_cycles=1)
+    assert r.iterations == k
+    assert r.matvecs == k                       # the last column is completed without a product
+    K = np.empty((n, k))
+    K[:, 0] = b
+    for i in range(1, k):
+        K[:, i] = A @ K[:, i - 1]
+    Q, _ = np.linalg.qr(K)
+    c = np.linalg.lstsq(A @ Q, b, rcond=None)[0]
+    assert np.allclose(r.x, Q @ c, rtol=1e-8, atol=1e-10)
+    assert abs(r.resid_est - np.linalg.norm(b - A @ r.x)) <= 1e-9 * np.linalg.norm(b)
+
+
+@pytest.mark.parametrize("m", [3, 8, 20])
+def test_dcgs2_iterates_equal_cgs2(rng, m):
+    """Same Krylov spaces, so the same restarted iteration: counts equal, iterates equal to rounding;
+    a cycle that converges before its last column costs one operator product more (the candidate after
+    the last completed column)."""
+    n = 60
+    A = _nonsym(rng, n, 2.0)
+    b = rng.standard_normal(n)
+    r1 = krylov.gmres(lambda v: A @ v, b, m=m, tol=1e-10, max_cycles=100)
+    r2 = krylov.gmres_dcgs2(lambda v: A @ v, b, m=m, tol=1e-10, max_cycles=100)
+    assert r1.converged and r2.converged
+    assert r2.iterations == r1.iterations
+    last = r1.iterations - m * ((r1.iterations - 1) // m)     # columns of the converged cycle
+    assert r2.matvecs == r1.matvecs + (1 if last < m else 0)
+    assert np.abs(r2.x - r1.x).max() <= 1e-9 * np.abs(r1.x).max()
+    assert np.linalg.norm(b - A @ r2.x) <= 1e-10 * np.linalg.norm(b) * 1.0001
+
+
+def test_dcgs2_keeps_orthogonality_where_one_pass_loses_it():
+    """A matrix with singular values spread over 1e-10..1: one classical Gram-Schmidt pass loses
+    orthogonality here, the delayed second pass must not; GMRES(n) then still reaches the dense solve."""
+    n = 40
+    rng = np.random.default_rng(5)
+    U, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    W, _ = np.linalg.qr(rng.standard_normal((n, n)))
+    A = U @ np.diag(np.logspace(0, -10, n)) @ W.T
+    b = A @ rng.standard_normal(n)
+    r = krylov.gmres_dcgs2(lambda v: A @ v, b, m=n, tol=1e-12, max_cycles=1)
+    r_ref = krylov.gmres(lambda v: A @ v, b, m=n, tol=1e-12, max_cycles=1)
+    assert np.linalg.norm(b - A @ r.x) <= 1e-10 * np.linalg.norm(b)
+    assert abs(r.iterations - r_ref.iterations) <= 1
+
+
+def test_dcgs2_newton_step_equals_cgs2():
+    """A Crank-Nicolson Allen-Cahn step solved with either Arnoldi form: same Newton and Krylov counts,
+    same state to rounding."""
+    from oracle import newton
+    import synthetic_inputs as si
+    n = 24
+    p = pdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    u0 = si.allen_cahn_ic(n, n, 1)
+    o1 = newton.Options(restart=10, tol_newton=1e-10, tol_krylov=1e-10)
+    o2 = newton.Options(restart=10, tol_newton=1e-10, tol_krylov=1e-10, ortho="dcgs2")
+    x1, r1 = newton.time_steps(p, u0, 1, o1)
+    x2, r2 = newton.time_steps(p, u0, 1, o2)
+    assert [r.newton_its for r in r1] == [r.newton_its for r in r2]
+    assert abs(sum(r.krylov_its for r in r1) - sum(r.krylov_its for r in r2)) <= 1
+    assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x1).max()
