@@ -58,6 +58,9 @@ def _args():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
     ap.add_argument("--no-fp64", action="store_true", help="skip the plain FP64 comparison run")
+    ap.add_argument("--ortho", default="dcgs2", choices=["cgs2", "dcgs2"],
+                    help="GMRES Arnoldi form of the timed run (the other form is timed beside it)")
+    ap.add_argument("--no-other-ortho", action="store_true", help="skip the run with the other Arnoldi form")
     ap.add_argument("--cpu-sample-iters", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true", help="skip the host-buffer end-to-end run")
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
@@ -337,15 +340,16 @@ def main() -> None:
     u0_dev = torch.tensor(u0, device="cuda")
     x = torch.empty_like(u0_dev)
 
-    def opts(form):
+    def opts(form, ortho=None):
         o = J.jfnk_default_opts(J.JFNK_MIXED_FP32 if form == "mixed" else J.JFNK_FP64)
         o.restart, o.tol_newton, o.tol_krylov = RESTART, TOL_NEWTON, TOL_KRYLOV[form]
         o.max_newton, o.max_krylov = 15, 100
+        o.ortho = J.JFNK_DCGS2 if (ortho or a.ortho) == "dcgs2" else J.JFNK_CGS2
         return o
 
-    def run_steps(form, k, timing=False):
+    def run_steps(form, k, timing=False, ortho=None):
         """k trajectory steps from u0; returns (event ms per step, reports, final x)."""
-        o = opts(form)
+        o = opts(form, ortho)
         J.jfnk_set_timing(ctx, timing)
         x.copy_(u0_dev)
         evs = [torch.cuda.Event(enable_timing=True) for _ in range(k + 1)]
@@ -422,6 +426,17 @@ def main() -> None:
                 "krylov_its": sum(r["krylov_its"] for r in reps64),
                 "max_rel_diff_mixed_vs_fp64": float((x_mixed - x64).abs().max() / x64.abs().max())}
 
+    # the same steps with the other Arnoldi form
+    other = None
+    if not a.no_other_ortho:
+        oth = "cgs2" if a.ortho == "dcgs2" else "dcgs2"
+        ms_o, reps_o, x_o = run_steps("mixed", a.steps, ortho=oth)
+        other = {"arnoldi": oth, "value": world * a.steps / (max_over_ranks(sum(ms_o)) / 1e3), "unit": "solves/s",
+                 "ms_per_step": sum(ms_o) / a.steps,
+                 "newton_its": sum(r["newton_its"] for r in reps_o),
+                 "krylov_its": sum(r["krylov_its"] for r in reps_o),
+                 "max_rel_diff_vs_timed": float((x_mixed - x_o).abs().max() / x_o.abs().max())}
+
     # end to end through the C ABI with host buffers: H2D of each step's input, D2H of its result
     e2e = None
     if not a.no_e2e:
@@ -451,12 +466,13 @@ def main() -> None:
         "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "steps_per_run": a.steps,
                    "form": "mixed: FP32 AD JVP + FP32 GMRES(40) basis, FP64 Newton residual/update/line search/"
                            "Hessenberg", "tol_newton": TOL_NEWTON, "tol_krylov": TOL_KRYLOV["mixed"],
+                   "arnoldi": a.ortho,
                    "l2": "inputs larger than L2 (GMRES basis 656 MB, state 32 MB per vector)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": p50, "p99_ms": p99,
         "newton_its": sum(r["newton_its"] for r in reps), "krylov_its": sum(r["krylov_its"] for r in reps),
         "jvp_gbs": jvp_gbs, "jvp_frac": (jvp_gbs / peak) if jvp_gbs else None,
-        "fp64_plain": fp64, "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches,
+        "fp64_plain": fp64, "other_arnoldi": other, "roofline": roofline, "kernels": kern, "gpu_launches": gpu_launches,
         "timed_with_kernel_events_ms_per_step": sum(ms_t) / a.steps,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "served": served,
     }

@@ -72,6 +72,14 @@ typedef enum {
   JFNK_MIXED_BF16 = 3   /* as MIXED_FP32 with the GMRES basis stored in BF16                  */
 } jfnk_precision;
 typedef enum { JFNK_EPS_SCALED = 0, JFNK_EPS_PAPER = 1 } jfnk_fd_rule;
+/* Arnoldi orthogonalisation of GMRES (Sec. 3): classical Gram-Schmidt applied
+ * twice, or the same two passes with the second one delayed by one Arnoldi
+ * step (delayed CGS2), which fuses them into one dots pass and one update
+ * pass over the basis. Same Krylov space, basis and iterates in exact
+ * arithmetic; each cycle that converges before its last column applies the
+ * Jacobian once more. DCGS2 runs on the streaming kernels: N (all fields) a
+ * multiple of 8, else JFNK_E_INVALID. The batched entry points use CGS2. */
+typedef enum { JFNK_CGS2 = 0, JFNK_DCGS2 = 1 } jfnk_ortho;
 
 /* One nonlinear problem: PDE, grid and time step (App. A and the benchmark
  * variants). The implicit step is the theta-method residual
@@ -102,6 +110,7 @@ typedef struct {
   double ls_c1;       /* Armijo constant: accept ||F(x+a dx)|| <= (1 - c1 a) ||F(x)|| */
   double ls_min_alpha;/* smallest trial step; accepted when no trial passes */
   int born_start;     /* Maxwell: solve the chi3 = 0 problem from zero first */
+  int ortho;          /* jfnk_ortho (GMRES) */
 } jfnk_opts;
 
 typedef struct {
@@ -116,7 +125,8 @@ typedef struct {
 
 /* Defaults of the paper for a precision (Sec. 3.3): tol_Newton 1e-6 / 1e-4,
  * tol_Krylov 1e-8 / 1e-6 (FP64 / FP32), 15 Newton iterations, 100 Krylov
- * cycles, GMRES(30), AD, scaled FD rule, c1 = 1e-4, alpha_min = 2^-10. */
+ * cycles, GMRES(30) with CGS2, AD, scaled FD rule, c1 = 1e-4,
+ * alpha_min = 2^-10. */
 void jfnk_default_opts(jfnk_opts* opts, int prec);
 
 /* Create a context on CUDA device `device`. hbm_budget caps the workspace

@@ -127,6 +127,7 @@ bool BatchEngine::supports(const jfnk_problem* pr, const jfnk_opts* o, std::stri
   if (!(o->tol_newton >= 0) || !(o->tol_krylov >= 0)) { if (why) *why = "bad tolerances"; return false; }
   if (!(o->ls_min_alpha > 0.0 && o->ls_min_alpha <= 1.0)) { if (why) *why = "bad ls_min_alpha"; return false; }
   if (o->fd_rule != JFNK_EPS_SCALED && o->fd_rule != JFNK_EPS_PAPER) { if (why) *why = "bad fd_rule"; return false; }
+  if (o->ortho != JFNK_CGS2) { if (why) *why = "batched solves use CGS2 Arnoldi"; return false; }
   return true;
 }
 

@@ -645,8 +645,7 @@ __global__ void __launch_bounds__(kBatThreads) k_batch(BatLaunch L) {
         const int nv = bat_nvals(S, ph);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int v = warp; v < nv; v += nw) {
-          double s = 0.0;
-          for (int u = lane; u < D.nunit; u += 32) s += __ldcg(D.part + (size_t)u * kBatPart + v);
+          double s = lane_strided_sum(D.part + v, kBatPart, D.nunit, lane);
           s = warp_sum(s);
           if (lane == 0) s_sum[v] = s;
         }

@@ -81,7 +81,7 @@ template <> struct arith_of<__nv_bfloat16> { typedef float type; };
 // ---------------------------------------------------------------------------
 constexpr int kVecThreads = 256;
 constexpr int kMaxVecBlocks = 608;          // 4 blocks per SM on 152 SMs
-constexpr int kMaxK = 72;                    // reductions of up to kMaxK values per launch
+constexpr int kMaxK = 136;                   // reductions of up to kMaxK values per launch
 
 inline int vec_blocks(long long n) {
   long long b = (n + kVecThreads * 4 - 1) / (kVecThreads * 4);
@@ -95,6 +95,27 @@ template <class A> __device__ __forceinline__ A warp_sum(A v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
   return v;
+}
+
+// sum over b = lane, lane + 32, ... < n of p[b * stride], added in that
+// order; the loads are issued eight at a time (partials written by other
+// blocks, read through L2) so the sum costs about one L2 round trip per 256
+// entries instead of one per eight.
+template <class A>
+__device__ __forceinline__ A lane_strided_sum(const A* p, size_t stride, int n, int lane) {
+  A s = A(0);
+  for (int b0 = 0; b0 < n; b0 += 256) {
+    A v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int b = b0 + lane + 32 * q;
+      v[q] = b < n ? __ldcg(p + (size_t)b * stride) : A(0);
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+      if (b0 + lane + 32 * q < n) s += v[q];
+  }
+  return s;
 }
 
 // Workspace of one reduction site: per-block partials and an arrival counter
@@ -142,8 +163,7 @@ __device__ __forceinline__ bool grid_reduce(A (&vals)[KMAX], int k, RedSite<A> s
   __threadfence();
   // last block: warp w sums value t = w, w + nwarps, ... over blocks, lane-strided, fixed order
   for (int t = warp; t < k; t += nwarps) {
-    A s = A(0);
-    for (int b = lane; b < nblocks; b += 32) s += __ldcg(&site.partials[(size_t)b * kMaxK + t]);
+    A s = lane_strided_sum(site.partials + t, kMaxK, nblocks, lane);
     s = warp_sum(s);
     if (lane == 0) fin(t, s);
   }

@@ -29,6 +29,13 @@ struct GmresCtl {
   double g[kMaxM + 1];             // rotated right-hand side beta e_1
   double y[kMaxM];                 // least-squares solution at the end of a cycle
   double scale[kMaxM + 1];         // v_t = scale[t] u_t
+  // delayed CGS2 (dcgs_step): completed columns before rotation, the first
+  // projection of the newest column, and the coefficients of the update pass
+  double Hraw[(kMaxM + 1) * kMaxM];
+  double hprev[kMaxM + 1];
+  double da[kMaxM + 1];            // q_j = dgamma u_j - sum_i da[i] q_i
+  double dc[kMaxM + 1];            // u_{j+1} = dinvr (w - sum_i dc[i] q_i - dc[j] q_j)
+  double dgamma, dinvr;
 };
 constexpr size_t kGmresHeadBytes = 4 * sizeof(double) + 8 * sizeof(int) + sizeof(void*);
 
@@ -114,6 +121,229 @@ __device__ __forceinline__ void gmres_givens_step(GmresCtl* c, int j, double n2)
     c->scale[j + 1] = 1.0 / hn;
   }
   mirror_active(c->host_active, c->active);
+}
+
+// gmres_givens_step run by every thread of a block: the column and the
+// previous rotations are staged in shared memory first, so thread 0's
+// sequential rotation reads shared memory instead of making one L2 round trip
+// per entry. Same arithmetic in the same order.
+__device__ __forceinline__ void gmres_givens_step_block(GmresCtl* c, int j, double n2) {
+  __shared__ double s_col[kMaxM + 1], s_cs[kMaxM], s_sn[kMaxM];
+  for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+    s_col[i] = c->h1[i] + c->h2[i];
+    if (i < j) { s_cs[i] = c->cs[i]; s_sn[i] = c->sn[i]; }
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double* col = c->H + (size_t)j * (kMaxM + 1);
+    const double hn = sqrt(n2);
+    s_col[j + 1] = hn;
+    for (int i = 0; i < j; ++i) {
+      const double a = s_col[i], b = s_col[i + 1];
+      s_col[i] = s_cs[i] * a + s_sn[i] * b;
+      s_col[i + 1] = -s_sn[i] * a + s_cs[i] * b;
+    }
+    const double f = s_col[j], gg = s_col[j + 1];
+    const double r = hypot(f, gg);
+    double cs = 1.0, sn = 0.0;
+    if (r != 0.0) { cs = f / r; sn = gg / r; }
+    c->cs[j] = cs;
+    c->sn[j] = sn;
+    s_col[j] = cs * f + sn * gg;
+    s_col[j + 1] = 0.0;
+    for (int i = 0; i <= j + 1; ++i) col[i] = s_col[i];
+    const double gj = c->g[j];
+    c->g[j + 1] = -sn * gj;
+    c->g[j] = cs * gj;
+    c->k = j + 1;
+    c->its += 1;
+    const double res = fabs(c->g[j + 1]);
+    c->resid = res;
+    if (!finite_d(res) || !finite_d(hn)) {
+      c->nonfinite = 1;
+      c->active = 0;
+    } else if (res <= c->target) {
+      c->converged = 1;
+      c->active = 0;
+    } else if (hn == 0.0) {
+      c->active = 0;
+    } else if (j + 1 >= c->m) {
+      c->active = 0;
+    } else {
+      c->scale[j + 1] = 1.0 / hn;
+    }
+    mirror_active(c->host_active, c->active);
+  }
+}
+
+// Delayed CGS2 (the second Gram-Schmidt pass of each Arnoldi vector one step
+// late), step j, run by every thread of one block after the fused dots pass.
+// Slot j of the basis holds the candidate u_j (projected once, not
+// normalised); the JVP was applied to ut = sigma u_j, sigma = scale[j], giving
+// w. S holds the pass's sums: S[2i] = q_i . u_j, S[2i+1] = q_i . w for i < j,
+// S[2j] = u_j . u_j, S[2j+1] = u_j . w (has_w = 0: the last step of a cycle,
+// no w). With s = sigma S[2i], rho^2 = sigma^2 S[2j] - s.s:
+//   * column j-1 is completed: H[:j, j-1] = hprev + s / sigma,
+//     H[j, j-1] = rho / sigma, then rotated and tested as in CGS2;
+//   * q_j = (ut - Q s) / rho, and the first projection of A q_j follows from
+//     w through the completed columns: z = H[:j+1, :j] s,
+//     h_i = (t_i - z_i) / rho (i < j), h_j = ((sigma S[2j+1] - s.t) / rho - z_j) / rho;
+//   * the update pass forms q_j and u_{j+1} = A q_j - Q_{j+1} h from the
+//     coefficients da, dc, dgamma, dinvr.
+// Everything the step reads is in shared memory: the caller stages the sums
+// S and the scalars, dcgs_stage stages the rest (the completed columns into
+// `hs`, which must hold j (kMaxM + 1) doubles) in the same round of loads, so
+// the sequential part makes no global round trips; sums over i are warp
+// butterflies, quotients are products with one reciprocal. sh must hold
+// 5 (kMaxM + 1) doubles.
+__device__ __forceinline__ void dcgs_stage(GmresCtl* c, int j, double* sh, double* hs) {
+  constexpr int LD = kMaxM + 1;
+  double* col = sh + 2 * LD;
+  const int cj = j - 1;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    col[i] = c->hprev[i];
+    if (i < cj) { sh[3 * LD + i] = c->cs[i]; sh[4 * LD + i] = c->sn[i]; }
+  }
+  for (int e = threadIdx.x; e < (j > 0 ? cj : 0) * LD; e += blockDim.x) hs[e] = __ldcg(&c->Hraw[e]);
+}
+
+__device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
+                                          double sigma, double g_prev, double target, int m, int active0) {
+  constexpr int LD = kMaxM + 1;
+  double* ss = sh;             // s
+  double* zz = sh + LD;        // z
+  double* col = sh + 2 * LD;   // column j-1: completed, then rotated
+  const double* s_cs = sh + 3 * LD;
+  const double* s_sn = sh + 4 * LD;
+  __shared__ int s_go;
+  __shared__ double s_rho, s_s2, s_st;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int cj = j - 1;
+  const double isig = 1.0 / sigma;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    const double si = sigma * S[2 * i];
+    ss[i] = si;
+    col[i] += si * isig;
+  }
+  __syncthreads();
+  if (warp == 0) {
+    double v = 0.0;
+    for (int i = lane; i < j; i += 32) v += ss[i] * ss[i];
+    v = warp_sum(v);
+    if (lane == 0) s_s2 = v;
+  } else if (warp == 1) {
+    double v = 0.0;
+    for (int i = lane; i < j; i += 32) v += ss[i] * S[2 * i + 1];
+    v = warp_sum(v);
+    if (lane == 0) s_st = v;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const double alpha = sigma * sigma * S[2 * j];
+    const double rho2 = alpha - s_s2;
+    const double rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
+    s_rho = rho;
+    int active = active0;
+    int go = 1;
+    if (!finite_d(rho2) || !finite_d(sigma)) {
+      c->nonfinite = 1;
+      active = 0;
+      go = 0;
+    } else if (j == 0) {
+      c->g[0] = g_prev * rho;      // r = beta rho q_0
+    } else {
+      // complete column j-1 (kept unrotated in Hraw) and rotate it
+      const double hn = rho * isig;
+      col[j] = hn;
+      for (int i = 0; i <= j; ++i) hs[(size_t)cj * LD + i] = col[i];
+      double a = col[0];
+      for (int i = 0; i < cj; ++i) {
+        const double b = col[i + 1];
+        col[i] = s_cs[i] * a + s_sn[i] * b;
+        a = -s_sn[i] * a + s_cs[i] * b;
+      }
+      const double f = a, gg = col[cj + 1];
+      const double r = hypot(f, gg);
+      double cs = 1.0, sn = 0.0;
+      if (r != 0.0) { const double ir = 1.0 / r; cs = f * ir; sn = gg * ir; }
+      c->cs[cj] = cs;
+      c->sn[cj] = sn;
+      col[cj] = cs * f + sn * gg;
+      col[cj + 1] = 0.0;
+      const double g1 = -sn * g_prev;
+      c->g[cj + 1] = g1;
+      c->g[cj] = cs * g_prev;
+      c->k = j;
+      c->its += 1;
+      const double res = fabs(g1);
+      c->resid = res;
+      if (!finite_d(res) || !finite_d(hn)) {
+        c->nonfinite = 1;
+        active = 0;
+      } else if (res <= target) {
+        c->converged = 1;
+        active = 0;
+      } else if (hn == 0.0 || j >= m) {   // lucky breakdown, or the end of the cycle
+        active = 0;
+      }
+      if (!active) go = 0;
+    }
+    if (go && has_w && rho == 0.0 && active) {   // the candidate vanished: nothing left to project
+      active = 0;
+      go = 0;
+    }
+    if (!has_w) go = 0;
+    if (!active) {
+      c->active = 0;
+      mirror_active(c->host_active, 0);
+    }
+    s_go = go;
+  }
+  __syncthreads();
+  // the completed column j-1 (unrotated and rotated) back to global memory
+  if (j > 0)
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      c->Hraw[(size_t)cj * LD + i] = hs[(size_t)cj * LD + i];
+      c->H[(size_t)cj * LD + i] = col[i];
+    }
+  if (!s_go) return;
+  const double rho = s_rho;
+  const double irho = 1.0 / rho;
+  // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg: warp per row
+  for (int i = warp; i <= j; i += nw) {
+    double z = 0.0;
+    for (int l = (i > 0 ? i - 1 : 0) + lane; l < j; l += 32) z += hs[(size_t)l * LD + i] * ss[l];
+    z = warp_sum(z);
+    if (lane == 0) zz[i] = z;
+  }
+  __syncthreads();
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    const double h = (S[2 * i + 1] - zz[i]) * irho;
+    c->hprev[i] = h;
+    c->da[i] = ss[i] * irho;
+    c->dc[i] = zz[i] + rho * h;
+  }
+  if (threadIdx.x == 0) {
+    const double qw = (sigma * S[2 * j + 1] - s_st) * irho;
+    const double h = (qw - zz[j]) * irho;
+    c->hprev[j] = h;
+    c->dc[j] = zz[j] + rho * h;
+    c->dgamma = sigma * irho;
+    c->dinvr = irho;
+  }
+}
+
+// After the update pass of step j: q_j is stored normalised, u_{j+1} has
+// squared norm n2.
+__device__ __forceinline__ void dcgs_after_update(GmresCtl* c, int j, double n2) {
+  c->scale[j] = 1.0;
+  if (!finite_d(n2)) {
+    c->nonfinite = 1;
+    c->active = 0;
+    mirror_active(c->host_active, 0);
+  } else {
+    c->scale[j + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  }
 }
 
 }  // namespace jfnk

@@ -1,0 +1,358 @@
+// dcgs_impl.cuh -- the two fused basis passes of delayed CGS2 (see dcgs_step in
+// ctl.cuh), instantiated per basis precision in stream_f64.cu, stream_f32.cu
+// and stream_bf16.cu:
+//   dots    q_i . u_j and q_i . w for i <= j (slot j holds u_j itself, so
+//           i = j gives u_j . u_j and u_j . w), then the step's scalar work
+//   update  q_j = dgamma u_j - sum_i da_i q_i (written over slot j),
+//           u_{j+1} = dinvr (w - sum_i dc_i q_i - dc_j q_j) (slot j + 1) and
+//           ||u_{j+1}||^2
+// Each reads basis slots 0..j and w once, against three passes of CGS2.
+// Resident form: one super-chunk of every vector involved fills one stage of a
+// two-stage shared-memory ring (bulk copies by producer warp 0, eight
+// consumer warps). Requires n % 8 == 0, like the other streaming passes.
+#pragma once
+
+#include "stream_impl.cuh"
+
+namespace jfnk {
+
+constexpr int kDcgsStages = 2;
+constexpr int kDcgsBudget = 100 * 1024;   // bytes per stage
+
+// bytes per vector of a super-chunk holding nv basis slots (+ the w chunk):
+// the largest power of two up to 32 KB whose stage fits the budget, so that
+// passes over few vectors still keep tens of kilobytes in flight per SM
+template <class TB, class TJ>
+static int dcgs_scb(int nv, bool has_w, int* stage) {
+  for (int scb = 32768; scb >= 512; scb >>= 1) {
+    const int ce = scb / (int)sizeof(TB);
+    int st = nv * scb + (has_w ? ce * (int)sizeof(TJ) : 0);
+    st = (st + 127) / 128 * 128;
+    if (st <= kDcgsBudget) { *stage = st; return scb; }
+  }
+  return 0;
+}
+
+// producer: slots 0..nv-1 of super-chunk `it`, then (w not null) the w chunk
+template <class TB, class TJ>
+__device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, const TJ* w, int nv, int CE,
+                                             int scb, int stage_bytes, unsigned char* sring, uint64_t* full,
+                                             uint64_t* empty, unsigned int* err, int* s_abort) {
+  const int lane = threadIdx.x & 31;
+  const int sidx = it % kDcgsStages;
+  if (it >= kDcgsStages &&
+      !mbar_wait_bounded(&empty[sidx], (uint32_t)(((it / kDcgsStages) - 1) & 1), kWaitLimitNs)) {
+    if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); *s_abort = 1; }
+    return false;
+  }
+  if (*s_abort) return false;
+  const long long e0 = ((long long)blockIdx.x + (long long)it * gridDim.x) * CE;
+  const long long rem = n - e0;
+  const int cnt = rem < CE ? (int)rem : CE;
+  const uint32_t vb = (uint32_t)cnt * sizeof(TB), wb = (uint32_t)cnt * sizeof(TJ);
+  unsigned char* st = sring + (size_t)sidx * stage_bytes;
+  if (lane == 0) mbar_arrive_expect_tx(&full[sidx], (uint32_t)nv * vb + (w ? wb : 0u));
+  __syncwarp();
+  for (int t = lane; t <= nv; t += 32) {
+    if (t < nv) bulk_g2s(st + (size_t)t * scb, V + (long long)t * n + e0, vb, &full[sidx]);
+    else if (w) bulk_g2s(st + (size_t)nv * scb, w + e0, wb, &full[sidx]);
+  }
+  __syncwarp();
+  return true;
+}
+
+// Dots pass. Consumer warps 1-4 accumulate q_i . u_j, warps 5-8 q_i . w:
+// each of the 128 threads of a group owns slices sl = t, t + 128, ... of
+// every chunk and keeps one accumulator per basis slot (the form of the
+// other streaming passes: all threads busy whatever j is). The last block to
+// finish sums the block partials and runs dcgs_step.
+template <class TB, class TJ, int KMAX>
+__global__ void __launch_bounds__(kStreamThreads + 32, 1)
+    k_dcgs_dots(long long n, const TB* __restrict__ V, int j, const TJ* __restrict__ w, GmresCtl* ctl,
+                double* partials, unsigned int* counter, int cap, int scb, int stage_bytes, unsigned int* err) {
+  typedef typename AccS<TJ>::type A;
+  constexpr int VW = 16 / (int)sizeof(TB);
+  constexpr int NA = KMAX + 1;                 // accumulators: basis slots 0..j, j <= KMAX
+  constexpr int GT = kStreamThreads / 2;       // threads per group
+  if (!ctl->active || (int)gridDim.x > cap) return;   // host sizing error: never write past the partials
+  extern __shared__ __align__(128) unsigned char sring[];
+  uint64_t* full = (uint64_t*)(sring + (size_t)kDcgsStages * stage_bytes);
+  uint64_t* empty = full + kDcgsStages;
+  __shared__ int s_abort;
+  __shared__ unsigned int s_last;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int q = 0; q < kDcgsStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kStreamThreads / 32);
+    }
+    fence_mbar_init();
+    s_abort = 0;
+  }
+  __syncthreads();
+  const int nv = j + 1;
+  const bool has_w = w != nullptr;
+  const int CE = scb / (int)sizeof(TB);
+  const long long nsc = (n + CE - 1) / CE;
+  const int my = ((long long)blockIdx.x < nsc) ? (int)((nsc - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  const int role = (warp - 1) >> 2;            // consumers: 0 dots with u_j, 1 dots with w
+  const int gt = ((warp - 1) & 3) * 32 + lane;
+  A acc[NA];
+#pragma unroll
+  for (int t = 0; t < NA; ++t) acc[t] = A(0);
+  if (warp == 0) {
+    int it = 0;
+    for (; it < my; ++it)
+      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, sring, full, empty, err, &s_abort)) break;
+    if (s_abort && lane == 0) {
+      for (int q = (it - kDcgsStages > 0 ? it - kDcgsStages : 0); q < it; ++q)
+        mbar_wait_bounded(&full[q % kDcgsStages], (uint32_t)((q / kDcgsStages) & 1), kWaitLimitNs);
+    }
+  } else {
+    for (int it = 0; it < my; ++it) {
+      const int sidx = it % kDcgsStages;
+      if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / kDcgsStages) & 1), kWaitLimitNs)) {
+        if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); s_abort = 1; }
+        break;
+      }
+      if (s_abort) break;
+      const long long e0 = ((long long)blockIdx.x + (long long)it * gridDim.x) * CE;
+      const long long rem = n - e0;
+      const int cnt = rem < CE ? (int)rem : CE;
+      const int nsl = cnt / VW;
+      const unsigned char* st = sring + (size_t)sidx * stage_bytes;
+      if (role == 0 || has_w) {
+        for (int sl = gt; sl < nsl; sl += GT) {
+          A x[VW];
+          if (role == 0) ld_slice<A, TB, VW>(x, (const TB*)(st + (size_t)j * scb) + sl * VW);
+          else ld_any<A, TJ, VW>(x, (const TJ*)(st + (size_t)nv * scb) + sl * VW);
+#pragma unroll
+          for (int t = 0; t < NA; ++t) {
+            if (t <= j) {
+              A q[VW];
+              ld_slice<A, TB, VW>(q, (const TB*)(st + (size_t)t * scb) + sl * VW);
+#pragma unroll
+              for (int e = 0; e < VW; ++e) acc[t] += q[e] * x[e];
+            }
+          }
+        }
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sidx]);
+    }
+  }
+  __syncthreads();
+  if (s_abort) return;
+  // block partials: warp butterflies, then the four warps of each group in order
+  __shared__ double red[kStreamThreads / 32][NA];
+  if (warp >= 1) {
+#pragma unroll
+    for (int t = 0; t < NA; ++t) {
+      if (t <= j) {
+        const A sv = warp_sum(acc[t]);
+        if (lane == 0) red[warp - 1][t] = (double)sv;
+      }
+    }
+  }
+  __syncthreads();
+  for (int v = tid; v < 2 * nv; v += blockDim.x) {
+    const int r = v & 1, t = v >> 1;
+    double sum = 0.0;
+#pragma unroll
+    for (int q = 0; q < 4; ++q) sum += red[4 * r + q][t];
+    partials[(size_t)blockIdx.x * kMaxK + v] = sum;
+  }
+  __threadfence();
+  __syncthreads();
+  if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
+  __syncthreads();
+  if (!s_last) return;
+  __threadfence();
+  __shared__ double S[2 * (kMaxM + 1)];
+  __shared__ double sh[5 * (kMaxM + 1)];
+  __shared__ double s_ctl[3];
+  __shared__ int s_m, s_active;
+  // one round of loads: every block's partials into the drained ring (when
+  // they fit beside the completed Hessenberg columns), the control state into
+  // shared memory
+  const int G = (int)gridDim.x, nval = 2 * nv;
+  const size_t ring = (size_t)kDcgsStages * stage_bytes;
+  const bool staged = ((size_t)G * nval + (size_t)j * (kMaxM + 1)) * sizeof(double) <= ring;
+  double* hs = (double*)sring;                       // completed Hessenberg columns
+  double* pr = hs + (size_t)j * (kMaxM + 1);         // [G][nval]
+  for (int e0 = tid; staged && e0 < G * nval; e0 += 8 * (int)blockDim.x) {
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      v[q] = e < G * nval ? __ldcg(&partials[(size_t)(e / nval) * kMaxK + (e % nval)]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      if (e < G * nval) pr[e] = v[q];
+    }
+  }
+  if (tid == 0) {
+    s_ctl[0] = ctl->scale[j];
+    s_ctl[1] = j > 0 ? ctl->g[j - 1] : ctl->g[0];
+    s_ctl[2] = ctl->target;
+    s_m = ctl->m;
+    s_active = ctl->active;
+  }
+  dcgs_stage(ctl, j, sh, hs);
+  __syncthreads();
+  // warp per value, lanes over blocks in a fixed order, then the butterfly
+  for (int v = warp; v < nval; v += (int)(blockDim.x >> 5)) {
+    double sum;
+    if (staged) {
+      sum = 0.0;
+      for (int b = lane; b < G; b += 32) sum += pr[(size_t)b * nval + v];
+    } else {
+      sum = lane_strided_sum(partials + v, kMaxK, G, lane);
+    }
+    sum = warp_sum(sum);
+    if (lane == 0) S[v] = sum;
+  }
+  __syncthreads();
+  dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[1], s_ctl[2], s_m, s_active);
+  __syncthreads();
+  if (tid == 0) *counter = 0u;
+}
+
+template <class TB, class TJ, int KMAX>
+__global__ void __launch_bounds__(kStreamThreads + 32, 1)
+    k_dcgs_update(long long n, TB* __restrict__ V, int j, const TJ* __restrict__ w, GmresCtl* ctl,
+                  RedSite<typename AccS<TJ>::type> red, int scb, int stage_bytes, unsigned int* err) {
+  typedef typename AccS<TJ>::type A;
+  constexpr int VW = 16 / (int)sizeof(TB);
+  if (!ctl->active) return;
+  extern __shared__ __align__(128) unsigned char sring[];
+  uint64_t* full = (uint64_t*)(sring + (size_t)kDcgsStages * stage_bytes);
+  uint64_t* empty = full + kDcgsStages;
+  __shared__ A ca[kMaxM + 1], cc[kMaxM + 1];
+  __shared__ A s_gamma, s_cj, s_invr;
+  __shared__ int s_abort;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  if (tid == 0) {
+    for (int q = 0; q < kDcgsStages; ++q) {
+      mbar_init(&full[q], 1);
+      mbar_init(&empty[q], kStreamThreads / 32);
+    }
+    fence_mbar_init();
+    s_abort = 0;
+    s_gamma = (A)ctl->dgamma;
+    s_cj = (A)ctl->dc[j];
+    s_invr = (A)ctl->dinvr;
+  }
+  for (int t = tid; t < j; t += blockDim.x) {
+    ca[t] = (A)ctl->da[t];
+    cc[t] = (A)ctl->dc[t];
+  }
+  __syncthreads();
+  const int nv = j + 1;
+  const int CE = scb / (int)sizeof(TB);
+  const long long nsc = (n + CE - 1) / CE;
+  const int my = ((long long)blockIdx.x < nsc) ? (int)((nsc - 1 - blockIdx.x) / gridDim.x + 1) : 0;
+  A acc[1] = {A(0)};
+  if (warp == 0) {
+    int it = 0;
+    for (; it < my; ++it)
+      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, sring, full, empty, err, &s_abort)) break;
+    if (s_abort && lane == 0) {
+      for (int q = (it - kDcgsStages > 0 ? it - kDcgsStages : 0); q < it; ++q)
+        mbar_wait_bounded(&full[q % kDcgsStages], (uint32_t)((q / kDcgsStages) & 1), kWaitLimitNs);
+    }
+  } else {
+    const A gam = s_gamma, cj = s_cj, invr = s_invr;
+    for (int it = 0; it < my; ++it) {
+      const int sidx = it % kDcgsStages;
+      if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / kDcgsStages) & 1), kWaitLimitNs)) {
+        if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); s_abort = 1; }
+        break;
+      }
+      if (s_abort) break;
+      const long long e0 = ((long long)blockIdx.x + (long long)it * gridDim.x) * CE;
+      const long long rem = n - e0;
+      const int cnt = rem < CE ? (int)rem : CE;
+      const unsigned char* st = sring + (size_t)sidx * stage_bytes;
+      for (int e = (tid - 32) * VW; e < cnt; e += kStreamThreads * VW) {   // this thread's slices of the chunk
+        A q[VW], y[VW];
+        ld_slice<A, TB, VW>(q, (const TB*)(st + (size_t)j * scb) + e);
+        ld_any<A, TJ, VW>(y, (const TJ*)(st + (size_t)nv * scb) + e);
+#pragma unroll
+        for (int i = 0; i < VW; ++i) q[i] *= gam;
+#pragma unroll
+        for (int t = 0; t < KMAX; ++t) {
+          if (t < j) {
+            A v[VW];
+            ld_slice<A, TB, VW>(v, (const TB*)(st + (size_t)t * scb) + e);
+            const A a = ca[t], c = cc[t];
+#pragma unroll
+            for (int i = 0; i < VW; ++i) {
+              q[i] -= a * v[i];
+              y[i] -= c * v[i];
+            }
+          }
+        }
+        // q_j as stored, then u_{j+1} from it
+#pragma unroll
+        for (int i = 0; i < VW; ++i) {
+          q[i] = as_arith<A>(store_as<TB>::cvt(q[i]));
+          y[i] = as_arith<A>(store_as<TB>::cvt((y[i] - cj * q[i]) * invr));
+          acc[0] += y[i] * y[i];
+        }
+        st_any<A, TB, VW>(V + (long long)j * n + e0 + e, q);
+        st_any<A, TB, VW>(V + (long long)(j + 1) * n + e0 + e, y);
+      }
+      __syncwarp();
+      if (lane == 0) mbar_arrive(&empty[sidx]);
+    }
+  }
+  __syncthreads();
+  if (s_abort) return;
+  __shared__ A sm[9];
+  __shared__ double s_n2;
+  const bool last = grid_reduce<A, 1>(acc, 1, red, gridDim.x, blockIdx.x, sm, [&](int, A sv) { s_n2 = (double)sv; });
+  if (last && tid == 0) dcgs_after_update(ctl, j, s_n2);
+}
+
+template <class TB, class TJ, int KMAX>
+static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
+                                 unsigned int* err, int nsm, cudaStream_t st) {
+  typedef typename AccS<TJ>::type A;
+  int stage = 0;
+  const int scb = dcgs_scb<TB, TJ>(j + 1, w != nullptr, &stage);
+  if (scb == 0) return cudaErrorInvalidValue;
+  const size_t smem = (size_t)kDcgsStages * stage + (size_t)kDcgsStages * 16;
+  static bool attr_set[2] = {false, false};
+  if (!attr_set[pass - 1]) {
+    cudaError_t e = pass == 1 ? cudaFuncSetAttribute(k_dcgs_dots<TB, TJ, KMAX>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     kDcgsStages * kDcgsBudget + 64)
+                              : cudaFuncSetAttribute(k_dcgs_update<TB, TJ, KMAX>,
+                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                                     kDcgsStages * kDcgsBudget + 64);
+    if (e != cudaSuccess) return e;
+    attr_set[pass - 1] = true;
+  }
+  if (pass == 1)
+    k_dcgs_dots<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
+        n, (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb, stage, err);
+  else
+    k_dcgs_update<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
+        n, (TB*)V, j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage, err);
+  return cudaGetLastError();
+}
+
+// pass 1: dots of step j (w null: the last step of a cycle); pass 2: update of step j
+template <class TB, class TJ>
+static cudaError_t dcgs_dispatch(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
+                                 unsigned int* err, int nsm, cudaStream_t st) {
+  if (j < 8) return dcgs_launch_k<TB, TJ, 8>(pass, n, V, j, w, ctl, red, err, nsm, st);
+  if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st);
+  if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st);
+  return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st);
+}
+
+}  // namespace jfnk

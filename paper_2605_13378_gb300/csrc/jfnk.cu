@@ -32,11 +32,12 @@ namespace {
 
 enum KClass {
   KC_RESIDUAL, KC_RHS, KC_JVP_AD, KC_JVP_FD, KC_ARN1, KC_ARN2, KC_ARN3, KC_GINIT, KC_GFIN, KC_CAST,
-  KC_VDOTS, KC_BICG, KC_COUNT
+  KC_VDOTS, KC_BICG, KC_DCGS1, KC_DCGS2, KC_COUNT
 };
 const char* kKClassNames[KC_COUNT] = {
     "residual", "rhs", "jvp_ad", "jvp_fd", "arnoldi_dots", "arnoldi_update_dots", "arnoldi_update_norm_givens",
-    "gmres_init", "gmres_backsolve_update", "cast", "vdots", "bicgstab_vector"};
+    "gmres_init", "gmres_backsolve_update", "cast", "vdots", "bicgstab_vector", "arnoldi_dcgs_dots",
+    "arnoldi_dcgs_update"};
 
 constexpr int kLookahead = 3;   // Arnoldi / BiCGSTAB steps the host may run ahead of the device
 
@@ -319,6 +320,49 @@ struct Solver {
     return JFNK_OK;
   }
 
+  // ---- one cycle of delayed-CGS2 Arnoldi: candidate u_j in basis slot j,
+  // JVP, fused dots (completes column j - 1), fused update (q_j, u_{j+1});
+  // the dots of u_m complete the last column. The device clears `active`
+  // when the cycle stops; kernels queued past that point return at once.
+  jfnk_status dcgs_cycle(int m, int* steps_run) {
+    jfnk_ctx::Ws& w = ctx->ws;
+    const double nv = (double)N;
+    int j = 0;
+    for (; j < m; ++j) {
+      if (j >= kLookahead) {
+        CK(cudaEventSynchronize(ctx->iter_ev[(j - kLookahead) % (kLookahead + 1)]), "iteration event");
+      }
+      if (*ctx->hflag == 0) break;
+      JvpArgs a = jvp_base();
+      a.v = (const char*)w.V + (size_t)j * N * sb();
+      a.tv = tb;
+      a.vscale = ctx->gctl->scale + j;
+      a.out = w.w;
+      a.active = &ctx->gctl->active;
+      jfnk_status s = jvp(a, j);
+      if (s) return s;
+      const double bs = (double)(j + 1) * nv * sb();
+      int ev1 = tm_begin(ctx, KC_DCGS1, bs + nv * sj(), j);
+      cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream);
+      tm_end(ctx, ev1);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs dots kernel");
+      int ev2 = tm_begin(ctx, KC_DCGS2, bs + nv * sj() + 2.0 * nv * sb(), j + 1);   // did work iff j < k
+      e = launch_dcgs(2, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream);
+      tm_end(ctx, ev2);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs update kernel");
+      CK(cudaEventRecord(ctx->iter_ev[j % (kLookahead + 1)], ctx->stream), "event record");
+    }
+    if (j == m) {   // the last column of the cycle
+      int ev1 = tm_begin(ctx, KC_DCGS1, (double)(m + 1) * nv * sb(), m);
+      cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, m, nullptr, ctx->gctl, ctx->red, ctx->derr, ctx->nsm,
+                                  ctx->stream);
+      tm_end(ctx, ev1);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs dots kernel");
+    }
+    *steps_run = j;
+    return JFNK_OK;
+  }
+
   // ---- restarted GMRES(m): J d = -F ------------------------------------
   jfnk_status gmres(int* kstatus) {
     jfnk_ctx::Ws& w = ctx->ws;
@@ -367,6 +411,34 @@ struct Solver {
           s = cast(tj, tb, w.w, w.V, 1.0);
           if (s) return s;
         }
+      }
+      if (o.ortho == JFNK_DCGS2) {
+        int steps_run = 0;
+        jfnk_status s = dcgs_cycle(m, &steps_run);
+        if (s) return s;
+        e = cudaSuccess;
+        if (steps_run > 0) {
+          int ev4 = tm_begin(ctx, KC_GFIN, 0.0, -1, 2);
+          e = launch_gmres_finish(tb, td, N, w.V, w.d, ctx->gctl, steps_run, ctx->stream, 1, ctx->derr, ctx->nsm);
+          tm_end(ctx, ev4);
+          if (e != cudaSuccess) return cuda_fail(ctx, e, "gmres update");
+        }
+        CK(cudaMemcpyAsync((char*)ctx->hbuf + 8192, ctx->derr, sizeof(unsigned), cudaMemcpyDeviceToHost, ctx->stream),
+           "read-back");
+        s = sync_read(ctx->gctl, kGmresHeadBytes);
+        if (s) return s;
+        GmresCtl head;
+        std::memcpy(&head, ctx->hbuf, kGmresHeadBytes);
+        unsigned derr = 0;
+        std::memcpy(&derr, (char*)ctx->hbuf + 8192, sizeof(unsigned));
+        if (derr) return fail(ctx, JFNK_E_TIMEOUT, "a bounded wait on a bulk copy expired in the Arnoldi kernels");
+        tm_harvest(ctx, head.k + 1, (double)head.k * nv * sb() + 2.0 * nv * vt_size(td));
+        // JVPs of the cycle: one per candidate, u_0 .. u_k (u_k only when the cycle stopped before its end)
+        rep.jvp_calls += (head.k < m ? head.k + 1 : m) + (cycle > 0 ? 1 : 0);
+        if (head.nonfinite) { rep.krylov_its += head.its; *kstatus = JFNK_E_NONFINITE; return JFNK_OK; }
+        if (head.converged) { rep.krylov_its += head.its; return JFNK_OK; }
+        if (cycle == o.max_krylov - 1) { rep.krylov_its += head.its; *kstatus = JFNK_E_NOT_CONVERGED; return JFNK_OK; }
+        continue;
       }
       int launched = 0;
       for (int j = 0; j < m; ++j) {
@@ -630,6 +702,7 @@ void jfnk_default_opts(jfnk_opts* o, int prec) {
   o->ls_c1 = 1e-4;
   o->ls_min_alpha = 1.0 / 1024.0;
   o->born_start = 1;
+  o->ortho = JFNK_CGS2;
 }
 
 jfnk_status jfnk_create(jfnk_ctx** out, int device, size_t hbm_budget, void* cuda_stream) {
@@ -782,6 +855,9 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
   if (!(o->tol_newton >= 0) || !(o->tol_krylov >= 0)) return fail(ctx, JFNK_E_INVALID, "bad tolerances");
   if (!(o->ls_min_alpha > 0.0 && o->ls_min_alpha <= 1.0)) return fail(ctx, JFNK_E_INVALID, "bad ls_min_alpha");
   if (o->fd_rule != JFNK_EPS_SCALED && o->fd_rule != JFNK_EPS_PAPER) return fail(ctx, JFNK_E_INVALID, "bad fd_rule");
+  if (o->ortho != JFNK_CGS2 && o->ortho != JFNK_DCGS2) return fail(ctx, JFNK_E_INVALID, "bad ortho");
+  if (o->krylov == JFNK_GMRES && o->ortho == JFNK_DCGS2 && !(ctx->stream_ok && stream_supported(ctx->N)))
+    return fail(ctx, JFNK_E_INVALID, "delayed CGS2 needs the streaming kernels (unknowns a multiple of 8)");
   return JFNK_OK;
 }
 

@@ -154,6 +154,15 @@ cudaError_t launch_basis_stream(int mode, int tb, int tj, int td, long long n, c
   return cudaErrorInvalidValue;
 }
 
+cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, const void* w, GmresCtl* ctl,
+                        RedWs red, unsigned int* err, int nsm, cudaStream_t st) {
+  if (!stream_supported(n) || j < 0 || j > kMaxM || (pass != 1 && pass != 2)) return cudaErrorInvalidValue;
+  if (tb == VT_F64 && tj == VT_F64) return dcgs_f64(pass, n, V, j, w, ctl, red, err, nsm, st);
+  if (tb == VT_F32 && tj == VT_F32) return dcgs_f32(pass, n, V, j, w, ctl, red, err, nsm, st);
+  if (tb == VT_BF16 && tj == VT_F32) return dcgs_bf16(pass, n, V, j, w, ctl, red, err, nsm, st);
+  return cudaErrorInvalidValue;
+}
+
 // back substitution H[:k,:k] y = g[:k] by one warp, column oriented
 __global__ void k_gmres_backsolve(GmresCtl* ctl) {
   const int k = ctl->k;

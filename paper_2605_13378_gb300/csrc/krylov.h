@@ -37,6 +37,18 @@ cudaError_t basis_stream_bf16(int mode, long long n, const void* V, int k, int k
 cudaError_t launch_basis_stream(int mode, int tb, int tj, int td, long long n, const void* V, int k, int kmax,
                                 void* w, void* d, GmresCtl* ctl, RedWs red, unsigned int* err, int nsm,
                                 cudaStream_t st);
+// Delayed CGS2 (dcgs_impl.cuh, ctl.cuh dcgs_step): pass 1 the fused dots of
+// Arnoldi step j over basis slots 0..j and w (w null: the last step of a
+// cycle, which only completes column j - 1), pass 2 the fused update of step
+// j. Requires stream_supported(n).
+cudaError_t dcgs_f64(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
+                     unsigned int* err, int nsm, cudaStream_t st);
+cudaError_t dcgs_f32(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
+                     unsigned int* err, int nsm, cudaStream_t st);
+cudaError_t dcgs_bf16(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
+                      unsigned int* err, int nsm, cudaStream_t st);
+cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, const void* w, GmresCtl* ctl,
+                        RedWs red, unsigned int* err, int nsm, cudaStream_t st);
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);
 cudaError_t launch_vdots(int t, long long n, int nd, const void* const* a, const void* const* b, double* sums,
                          RedWs red, const int* active, cudaStream_t st);

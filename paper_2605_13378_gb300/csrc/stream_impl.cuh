@@ -288,7 +288,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     __shared__ double s_n2;
     const bool last = grid_reduce<A, NACC>(acc, 1, red, gridDim.x, blockIdx.x, sm,
                                            [&](int, A sv) { s_n2 = (double)sv; });
-    if (last && tid == 0) gmres_givens_step(ctl, k - 1, s_n2);
+    if (last) gmres_givens_step_block(ctl, k - 1, s_n2);
   }
 }
 

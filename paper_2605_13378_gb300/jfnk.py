@@ -28,6 +28,7 @@ JFNK_GMRES, JFNK_BICGSTAB, JFNK_CG = 0, 1, 2
 JFNK_BURGERS1D, JFNK_ALLEN_CAHN2D, JFNK_SU_OLSON2D, JFNK_MAXWELL_TE2D = 0, 1, 2, 3
 JFNK_FP64, JFNK_FP32, JFNK_MIXED_FP32, JFNK_MIXED_BF16 = 0, 1, 2, 3
 JFNK_EPS_SCALED, JFNK_EPS_PAPER = 0, 1
+JFNK_CGS2, JFNK_DCGS2 = 0, 1
 JFNK_MAX_RESTART = 64
 
 EXPORTED = ["jfnk_default_opts", "jfnk_create", "jfnk_set_problem", "jfnk_jvp", "jfnk_residual", "jfnk_solve",
@@ -45,7 +46,7 @@ class jfnk_opts(C.Structure):
     _fields_ = [("lin", C.c_int), ("krylov", C.c_int), ("prec", C.c_int), ("restart", C.c_int),
                 ("max_newton", C.c_int), ("max_krylov", C.c_int), ("tol_newton", C.c_double),
                 ("tol_krylov", C.c_double), ("fd_rule", C.c_int), ("fd_eps", C.c_double), ("ls_c1", C.c_double),
-                ("ls_min_alpha", C.c_double), ("born_start", C.c_int)]
+                ("ls_min_alpha", C.c_double), ("born_start", C.c_int), ("ortho", C.c_int)]
 
 
 class jfnk_report(C.Structure):

@@ -1,0 +1,197 @@
+"""GMRES with delayed CGS2 Arnoldi (opts.ortho = JFNK_DCGS2) against the oracle (GPU).
+
+Delayed CGS2 applies the two classical Gram-Schmidt passes of CGS2 with the
+second one a step late, so that one fused dots pass and one fused update pass
+over the basis serve each Arnoldi step. In exact arithmetic it produces the
+CGS2 basis, Hessenberg matrix and iterates, so the parity bar is the one of
+the CGS2 solves: each case is solved through jfnk_solve and by the oracle's
+delayed-CGS2 GMRES (oracle.krylov.gmres_dcgs2) on the same seeded input;
+solutions agree to 1e-10 relative (FP64) or 1e-5 (reduced precision), Newton
+counts are equal in FP64 and Krylov counts lie within 2 per Newton step (the
+reduction order differs from the oracle's), or inside the oracle's own
+perturbation band for the radiation problem. The GPU's CGS2 and delayed-CGS2
+solves of the same problem must agree to the same tolerance, and restart
+lengths 1 and 64, the benchmark grid and the size restriction are covered.
+"""
+import json
+import os
+
+import numpy as np
+import pytest
+
+import synthetic_inputs as si
+from oracle import newton as onw, pdes as opdes
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def J():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    from paper_2605_13378_gb300 import build
+    build.build()
+    from paper_2605_13378_gb300 import jfnk
+    return jfnk
+
+
+@pytest.fixture
+def ctx(J):
+    c = J.jfnk_create(0)
+    yield c
+    J.jfnk_destroy(c)
+
+
+def _opts(J, prec, lin="ad", restart=30, tol_n=1e-10, tol_k=1e-10, max_newton=15, max_krylov=100, ortho=None):
+    o = J.jfnk_default_opts(prec)
+    o.lin = J.JFNK_AD if lin == "ad" else J.JFNK_FD
+    o.restart, o.tol_newton, o.tol_krylov = restart, tol_n, tol_k
+    o.max_newton, o.max_krylov = max_newton, max_krylov
+    o.ortho = J.JFNK_DCGS2 if ortho is None else ortho
+    return o
+
+
+def _oopts(lin="ad", restart=30, tol_n=1e-10, tol_k=1e-10, max_newton=15, max_krylov=100):
+    return onw.Options(lin=lin, krylov="gmres", restart=restart, tol_newton=tol_n, tol_krylov=tol_k,
+                       max_newton=max_newton, max_cycles=max_krylov, ortho="dcgs2")
+
+
+def _run(J, ctx, lp, opts, x0, steps):
+    J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+    x = torch.tensor(x0, device="cuda")
+    rep = J.jfnk_report()
+    s = J.jfnk_solve(ctx, opts, None, x, steps, rep)
+    torch.cuda.synchronize()
+    return s, x.cpu().numpy(), rep
+
+
+def _compare(x, x_ref, rep, reps, tol_x, band=None):
+    err = np.abs(x - x_ref).max() / np.abs(x_ref).max()
+    assert err <= tol_x, err
+    nn = sum(r.newton_its for r in reps)
+    assert rep.newton_its == nn, (rep.newton_its, nn)
+    kk = sum(r.krylov_its for r in reps)
+    if band is None:
+        assert abs(rep.krylov_its - kk) <= 2 * max(nn, 1), (rep.krylov_its, kk)
+    else:
+        lo, hi = band
+        assert 0.9 * lo - 2 * nn <= rep.krylov_its <= 1.1 * hi + 2 * nn, (rep.krylov_its, band)
+
+
+@pytest.mark.parametrize("lin", ["ad", "fd"])
+def test_allen_cahn_two_steps_fp64(J, ctx, lin):
+    n = 72
+    u0 = si.allen_cahn_ic(n, n, 3)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, lin, 40), u0, 2)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 2, _oopts(lin, 40))
+    _compare(x, x_ref, rep, reps, 1e-10)
+    # the CGS2 solve of the same problem on the GPU
+    s2, x2, rep2 = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, lin, 40, ortho=J.JFNK_CGS2), u0, 2)
+    assert s2 == J.JFNK_OK
+    assert np.abs(x - x2).max() <= 1e-10 * np.abs(x2).max()
+    assert rep.newton_its == rep2.newton_its and abs(rep.krylov_its - rep2.krylov_its) <= 2 * rep.newton_its
+
+
+def test_burgers_1024_fp64(J, ctx):
+    N = 1024
+    u0 = si.burgers_ic(N, 0)
+    p = opdes.Burgers1D(N=N, nu=1e-2, dt=1e-3)
+    lp = J.make_problem("burgers1d", N, 1, 1e-3, 1.0, (1e-2,))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts())
+    _compare(x, x_ref, rep, reps, 1e-10)
+    assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-10 * reps[0].res0
+
+
+def test_su_olson_fp64(J, ctx):
+    n = 40
+    x0 = si.su_olson_ic(n, n)
+    p = opdes.SuOlson2D(nx=n, ny=n, dt=1e-3, theta=0.5)
+    lp = J.make_problem("su_olson", n, n, 1e-3, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, "ad", 30, 1e-9, 1e-10), x0, 2)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    run = lambda xs: onw.time_steps(p, xs, 2, _oopts("ad", 30, 1e-9, 1e-10))[1]
+    x_ref, reps = onw.time_steps(p, x0, 2, _oopts("ad", 30, 1e-9, 1e-10))
+    counts = []
+    for seed in range(5):
+        xp = x0 if seed == 0 else x0 * (1 + 1e-15 * np.random.default_rng(seed).standard_normal(x0.size))
+        counts.append(sum(r.krylov_its for r in run(xp)))
+    _compare(x, x_ref, rep, reps, 1e-10, band=(min(counts), max(counts)))
+
+
+def test_maxwell_born_fp64(J, ctx):
+    n, k, chi = 16, 3.0, 0.1
+    eps, f = si.maxwell_medium(n, n, 0), si.maxwell_point_source(n, n)
+    p = opdes.MaxwellTE2D(nx=n, ny=n, k=k, chi3=chi, eps_r=eps, f=f)
+    lp = J.make_problem("maxwell", n, n, 0.0, 1.0, (k, chi), eps_r=eps, source=f)
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, "ad", 60, 1e-8, 1e-8, 50, 30), np.zeros(2 * n * n), 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, oref, _ = onw.bvp_solve(p, _oopts("ad", 60, 1e-8, 1e-8, 50, 30))
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-8
+    assert rep.newton_its == oref.newton_its
+
+
+@pytest.mark.parametrize("prec", ["mixed", "bf16", "fp32"])
+def test_allen_cahn_reduced_precision(J, ctx, prec):
+    n = 72
+    u0 = si.allen_cahn_ic(n, n, 5)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    code = {"mixed": J.JFNK_MIXED_FP32, "bf16": J.JFNK_MIXED_BF16, "fp32": J.JFNK_FP32}[prec]
+    tol_n = 1e-4 if prec == "fp32" else 1e-9
+    tol_k = 1e-5 if prec != "bf16" else 1e-2
+    s, x, rep = _run(J, ctx, lp, _opts(J, code, "ad", 40, tol_n, tol_k, max_newton=30), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts("ad", 40, 1e-12, 1e-12))
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5
+    if prec != "fp32":
+        assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= tol_n * reps[0].res0 * 1.0001
+
+
+@pytest.mark.parametrize("m", [1, 64])
+def test_extreme_restart_lengths(J, ctx, m):
+    n = 48
+    u0 = si.allen_cahn_ic(n, n, 2)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    tol_k = 1e-10 if m == 64 else 1e-6
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, restart=m, tol_k=tol_k, max_krylov=2000), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts(restart=m, tol_k=tol_k, max_krylov=2000))
+    _compare(x, x_ref, rep, reps, 1e-9)
+
+
+def test_size_restriction_and_bicgstab_ignores_it(J, ctx):
+    lp = J.make_problem("allen_cahn", 30, 31, 0.1, 0.5, (1e-3, 1.0))     # 930 unknowns: not a multiple of 8
+    J.check(ctx, J.jfnk_set_problem(ctx, lp), "set")
+    x = np.zeros(930) + 0.01
+    assert J.jfnk_solve(ctx, _opts(J, J.JFNK_FP64), None, x, 1, None) == J.JFNK_E_INVALID
+    assert "multiple of 8" in J.jfnk_last_error(ctx)
+    o = _opts(J, J.JFNK_FP64)
+    o.krylov = J.JFNK_BICGSTAB
+    assert J.jfnk_solve(ctx, o, None, x, 1, None) == J.JFNK_OK
+    o = _opts(J, J.JFNK_FP64)
+    o.ortho = 7
+    assert J.jfnk_solve(ctx, o, None, x, 1, None) == J.JFNK_E_INVALID
+
+
+def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
+    """The benchmark grid in FP64 with delayed CGS2 against the oracle's stored (CGS2) solve: the two
+    Arnoldi forms are the same method, so the stored counts and values bind."""
+    g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "allen_cahn_2048_step1.json")))
+    n = 2048
+    u0 = si.allen_cahn_ic(n, n, 0)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, "ad", 40, 1e-8, 1e-8), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    assert rep.newton_its == g["newton_its"]
+    assert abs(rep.krylov_its - g["krylov_its"]) <= 2 * g["newton_its"], (rep.krylov_its, g["krylov_its"])
+    assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-8 * g["res0"]
+    xs = np.array([x[i] for i in g["sample_idx"]])
+    assert np.abs(xs - np.array(g["x_samples"])).max() <= 1e-9 * g["x_absmax"]

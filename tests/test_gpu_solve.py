@@ -216,7 +216,7 @@ def test_max_restart_and_invalid_options(J, ctx):
 
 
 def test_hbm_budget_is_enforced(J):
-    c = J.jfnk_create(0, 1 << 20)
+    c = J.jfnk_create(0, 4 << 20)       # room for the reduction workspace, not for a 512^2 solve
     try:
         n = 512
         J.check(c, J.jfnk_set_problem(c, J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))), "set")
