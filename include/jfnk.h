@@ -55,6 +55,12 @@ typedef enum {
 } jfnk_status;
 
 typedef enum { JFNK_AD = 0, JFNK_FD = 1 } jfnk_linearisation;
+/* Krylov solver of the Newton system J d = -F (Sec. 3): restarted GMRES,
+ * BiCGSTAB, or conjugate gradients, which needs J symmetric positive definite
+ * (the reaction-diffusion / Allen-Cahn implicit step with theta dt small
+ * enough; not the radiation, Burgers or Maxwell Jacobians). CG applies one
+ * JVP per iteration with the p.Jp dot fused into it; a non-positive or
+ * non-finite p.Jp ends it with JFNK_E_BREAKDOWN. */
 typedef enum { JFNK_GMRES = 0, JFNK_BICGSTAB = 1, JFNK_CG = 2 } jfnk_krylov;
 typedef enum {
   JFNK_BURGERS1D = 0,     /* p[0] = nu                                              */

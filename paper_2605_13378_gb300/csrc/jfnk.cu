@@ -557,6 +557,57 @@ struct Solver {
     return JFNK_OK;
   }
 
+  // ---- conjugate gradients: J d = -F (J symmetric positive definite) ----
+  jfnk_status cg(int* kstatus) {
+    jfnk_ctx::Ws& w = ctx->ws;
+    BicgVecs vv;
+    vv.F = F; vv.r = w.r; vv.rhat = nullptr; vv.p = w.p; vv.v = w.v; vv.s = nullptr; vv.t = nullptr; vv.d = w.d;
+    vv.sums = sc; vv.sn2 = nullptr;
+    const double nv = (double)N, s_ = (double)sj();
+    const bool fd_norms = (o.lin == 1 && o.fd_eps <= 0 && o.fd_rule == JFNK_EPS_SCALED);
+    vv.pn2 = fd_norms ? ctx->dsc + 12 : nullptr;
+    *ctx->hflag = 1;
+    int ev = tm_begin(ctx, KC_BICG, nv * (ss() + 2 * s_ + ss()), -1);
+    cudaError_t e = launch_cg(0, ts, tj, td, N, vv, ctx->bctl, ctx->red, 0, o.tol_krylov, ctx->stream);
+    tm_end(ctx, ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cg init");
+    *kstatus = 0;
+    for (int it = 0; it < o.max_krylov; ++it) {
+      if (it >= kLookahead) {
+        CK(cudaEventSynchronize(ctx->iter_ev[(it - kLookahead) % (kLookahead + 1)]), "iteration event");
+      }
+      if (*ctx->hflag == 0) break;
+      if (it > 0) {
+        int e1 = tm_begin(ctx, KC_BICG, nv * 3 * s_, it);
+        e = launch_cg(1, ts, tj, td, N, vv, ctx->bctl, ctx->red, it, o.tol_krylov, ctx->stream);
+        tm_end(ctx, e1);
+        if (e != cudaSuccess) return cuda_fail(ctx, e, "cg p");
+      }
+      JvpArgs a = jvp_base();
+      a.v = w.p; a.out = w.v; a.ndots = 1; a.dw[0] = w.p; a.sums = ctx->bctl->sums;
+      a.active = &ctx->bctl->active;
+      if (fd_norms) a.vn2 = vv.pn2;
+      jfnk_status s = jvp(a, it);
+      if (s) return s;
+      int e2 = tm_begin(ctx, KC_BICG, nv * (4 * s_ + 2 * ss()), it);
+      e = launch_cg(2, ts, tj, td, N, vv, ctx->bctl, ctx->red, it, o.tol_krylov, ctx->stream);
+      tm_end(ctx, e2);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "cg update");
+      CK(cudaEventRecord(ctx->iter_ev[it % (kLookahead + 1)], ctx->stream), "event record");
+    }
+    jfnk_status s = sync_read(ctx->bctl, sizeof(BicgCtl));
+    if (s) return s;
+    BicgCtl c;
+    std::memcpy(&c, ctx->hbuf, sizeof(BicgCtl));
+    tm_harvest(ctx, c.its, -1.0);
+    rep.krylov_its += c.its;
+    rep.jvp_calls += c.its;
+    if (c.nonfinite) *kstatus = JFNK_E_NONFINITE;
+    else if (c.breakdown) *kstatus = JFNK_E_BREAKDOWN;
+    else if (!c.converged) *kstatus = JFNK_E_NOT_CONVERGED;
+    return JFNK_OK;
+  }
+
   // ---- one nonlinear solve F(x; b) = 0 from the current x ---------------
   // denom > 0 overrides ||F(x0)|| as the Eq. 5 denominator.
   jfnk_status newton(int* nstatus, double denom, bool linear_once) {
@@ -580,7 +631,7 @@ struct Solver {
         if (s) return s;
       }
       int kst = 0;
-      s = (o.krylov == JFNK_BICGSTAB) ? bicgstab(&kst) : gmres(&kst);
+      s = (o.krylov == JFNK_BICGSTAB) ? bicgstab(&kst) : (o.krylov == JFNK_CG ? cg(&kst) : gmres(&kst));
       if (s) return s;
       if (kst == JFNK_E_BREAKDOWN || kst == JFNK_E_NONFINITE) { *nstatus = kst; break; }
       if (kst == JFNK_E_NOT_CONVERGED) rep.krylov_failures += 1;
@@ -845,11 +896,11 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
   int ts, tj, tb;
   if (!prec_types(o->prec, &ts, &tj, &tb)) return fail(ctx, JFNK_E_INVALID, "bad precision");
   if (o->lin != JFNK_AD && o->lin != JFNK_FD) return fail(ctx, JFNK_E_INVALID, "bad linearisation");
-  if (o->krylov != JFNK_GMRES && o->krylov != JFNK_BICGSTAB)
-    return fail(ctx, JFNK_E_INVALID, "krylov must be GMRES or BiCGSTAB");
+  if (o->krylov != JFNK_GMRES && o->krylov != JFNK_BICGSTAB && o->krylov != JFNK_CG)
+    return fail(ctx, JFNK_E_INVALID, "krylov must be GMRES, BiCGSTAB or CG");
   if (o->krylov == JFNK_GMRES && (o->restart < 1 || o->restart > JFNK_MAX_RESTART))
     return fail(ctx, JFNK_E_INVALID, "restart out of range");
-  if (o->krylov == JFNK_BICGSTAB && o->prec == JFNK_MIXED_BF16)
+  if (o->krylov != JFNK_GMRES && o->prec == JFNK_MIXED_BF16)
     return fail(ctx, JFNK_E_INVALID, "BF16 storage applies to the GMRES basis only");
   if (o->max_newton < 0 || o->max_krylov < 1) return fail(ctx, JFNK_E_INVALID, "bad iteration limits");
   if (!(o->tol_newton >= 0) || !(o->tol_krylov >= 0)) return fail(ctx, JFNK_E_INVALID, "bad tolerances");

@@ -468,6 +468,118 @@ cudaError_t launch_vdots(int t, long long n, int nd, const void* const* a, const
   return cudaGetLastError();
 }
 
+// ---------------------------------------------------------------------------
+// Conjugate gradients (Hestenes-Stiefel) for symmetric positive definite
+// Jacobians, x_0 = 0. Scalars live in BicgCtl: rho = r.r, alpha, beta;
+// sums[0] = p.q from the JVP's fused dot. Every phase first checks `active`.
+// ---------------------------------------------------------------------------
+// init: r = p = b = -F (TJ), d = 0; rho = ||b||^2 (= ||p||^2 for the FD step)
+template <class TS, class TJ, class TD>
+__global__ void k_cg_init(long long n, const TS* __restrict__ F, TJ* r, TJ* p, TD* d, BicgCtl* c,
+                          const double* sums, double* pn2, double tol) {
+  VEC_LOOP(i, n) {
+    const TJ b = (TJ)(-F[i]);
+    r[i] = b; p[i] = b; d[i] = TD(0);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    const double bn = sqrt(sums[0]);
+    c->bnorm = bn;
+    c->target = tol * bn;
+    c->rho = sums[0];
+    c->beta = 0.0;
+    c->its = 0; c->converged = 0; c->breakdown = 0; c->nonfinite = 0; c->flag_half = 0;
+    c->resid = bn;
+    c->active = (bn > 0.0 && isfinite(bn)) ? 1 : 0;
+    if (bn == 0.0) c->converged = 1;
+    if (!isfinite(bn)) c->nonfinite = 1;
+    if (pn2) *pn2 = sums[0];
+    mirror_active(c->host_active, c->active);
+  }
+}
+
+// p = r + beta p (iterations after the first); ||p||^2 for the FD step
+template <class TJ>
+__global__ void __launch_bounds__(256) k_cg_p(long long n, const TJ* __restrict__ r, TJ* __restrict__ p, BicgCtl* c,
+                                              double* pn2, RedSite<typename AccK<TJ>::type> red) {
+  typedef typename AccK<TJ>::type A;
+  if (!c->active) return;
+  const A beta = (A)c->beta;
+  A acc[1] = {A(0)};
+  VEC_LOOP(i, n) {
+    const A pi = (A)r[i] + beta * (A)p[i];
+    p[i] = (TJ)pi;
+    acc[0] += pi * pi;
+  }
+  if (pn2) {
+    __shared__ A sm[8];
+    grid_reduce<A, 1>(acc, 1, red, gridDim.x, blockIdx.x, sm, [&](int, A s) { *pn2 = (double)s; });
+  }
+}
+
+// after q = J p with sums[0] = p.q: alpha = rho / (p.q); d += alpha p; r -= alpha q;
+// rho' = r.r; converged on ||r|| <= target, else beta = rho' / rho
+template <class TJ, class TD>
+__global__ void __launch_bounds__(256) k_cg_x(long long n, const TJ* __restrict__ p, const TJ* __restrict__ q,
+                                              TJ* __restrict__ r, TD* __restrict__ d, BicgCtl* c,
+                                              RedSite<typename AccK<TJ>::type> red, int it) {
+  typedef typename AccK<TJ>::type A;
+  if (!c->active) return;
+  const double pq = c->sums[0];
+  const bool bad = !(pq > 0.0) || !isfinite(pq);   // J not positive definite along p
+  const double alpha = bad ? 0.0 : c->rho / pq;
+  const A al = (A)alpha;
+  A acc[1] = {A(0)};
+  if (!bad) {
+    VEC_LOOP(i, n) {
+      d[i] = d[i] + (TD)(al * (A)p[i]);
+      const A ri = (A)r[i] - al * (A)q[i];
+      r[i] = (TJ)ri;
+      acc[0] += ri * ri;
+    }
+  }
+  __shared__ A sm[8];
+  __shared__ double s_r2;
+  const bool last = grid_reduce<A, 1>(acc, 1, red, gridDim.x, blockIdx.x, sm, [&](int, A v) { s_r2 = (double)v; });
+  if (last && threadIdx.x == 0) {
+    c->its = it + 1;
+    if (bad) {
+      c->breakdown = 1; c->active = 0;
+    } else {
+      c->alpha = alpha;
+      const double rn = sqrt(s_r2);
+      c->resid = rn;
+      if (!isfinite(rn)) { c->nonfinite = 1; c->active = 0; }
+      else if (rn <= c->target) { c->converged = 1; c->active = 0; }
+      else { c->beta = s_r2 / c->rho; c->rho = s_r2; }
+    }
+    mirror_active(c->host_active, c->active);
+  }
+}
+
+cudaError_t launch_cg(int phase, int ts, int tj, int td, long long n, const BicgVecs& vv, BicgCtl* c, RedWs red,
+                      int it, double tol, cudaStream_t st) {
+  const int nb = vec_blocks(n);
+#define CGK(TS_, TJ_, TD_)                                                                                  \
+  do {                                                                                                      \
+    typedef typename AccK<TJ_>::type A;                                                                     \
+    RedSite<A> rs{(A*)red.partials, red.counter, red.max_blocks};                                           \
+    switch (phase) {                                                                                        \
+      case 0: k_cg_init<TS_, TJ_, TD_><<<nb, kVecThreads, 0, st>>>(n, (const TS_*)vv.F, (TJ_*)vv.r,         \
+                  (TJ_*)vv.p, (TD_*)vv.d, c, vv.sums, vv.pn2, tol); break;                                  \
+      case 1: k_cg_p<TJ_><<<nb, kVecThreads, 0, st>>>(n, (const TJ_*)vv.r, (TJ_*)vv.p, c, vv.pn2, rs);      \
+              break;                                                                                        \
+      case 2: k_cg_x<TJ_, TD_><<<nb, kVecThreads, 0, st>>>(n, (const TJ_*)vv.p, (const TJ_*)vv.v,           \
+                  (TJ_*)vv.r, (TD_*)vv.d, c, rs, it); break;                                                \
+    }                                                                                                       \
+  } while (0)
+  if (ts == VT_F64 && tj == VT_F64 && td == VT_F64) CGK(double, double, double);
+  else if (ts == VT_F32 && tj == VT_F32 && td == VT_F32) CGK(float, float, float);
+  else if (ts == VT_F64 && tj == VT_F32 && td == VT_F64) CGK(double, float, double);
+  else return cudaErrorInvalidValue;
+#undef CGK
+  return cudaGetLastError();
+}
+
 cudaError_t launch_bicg(int phase, int ts, int tj, int td, long long n, const BicgVecs& vv, BicgCtl* c,
                         RedWs red, int it, double tol, cudaStream_t st) {
   const int nb = vec_blocks(n);

@@ -52,6 +52,11 @@ cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, c
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);
 cudaError_t launch_vdots(int t, long long n, int nd, const void* const* a, const void* const* b, double* sums,
                          RedWs red, const int* active, cudaStream_t st);
+// CG: phase 0 init (r = p = -F, d = 0), 1 p = r + beta p (not in the first
+// iteration), 2 after q = J p (vv.v) with p.q in c->sums[0]: x, r update,
+// convergence, beta. vv.pn2 (may be null) gets ||p||^2 for the FD step.
+cudaError_t launch_cg(int phase, int ts, int tj, int td, long long n, const BicgVecs& vv, BicgCtl* c, RedWs red,
+                      int it, double tol, cudaStream_t st);
 // phase 0 init, 1 p-update, 2 s-update, 3 half-step x update, 4 x/r update
 cudaError_t launch_bicg(int phase, int ts, int tj, int td, long long n, const BicgVecs& vv, BicgCtl* c,
                         RedWs red, int it, double tol, cudaStream_t st);

@@ -47,7 +47,7 @@ def ctx(J):
 def _opts(J, prec, lin="ad", krylov="gmres", restart=30, tol_n=1e-10, tol_k=1e-10, max_newton=15, max_krylov=100):
     o = J.jfnk_default_opts(prec)
     o.lin = J.JFNK_AD if lin == "ad" else J.JFNK_FD
-    o.krylov = J.JFNK_GMRES if krylov == "gmres" else J.JFNK_BICGSTAB
+    o.krylov = {"gmres": J.JFNK_GMRES, "bicgstab": J.JFNK_BICGSTAB, "cg": J.JFNK_CG}[krylov]
     o.restart, o.tol_newton, o.tol_krylov = restart, tol_n, tol_k
     o.max_newton, o.max_krylov = max_newton, max_krylov
     return o
@@ -245,3 +245,34 @@ def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
     xs = np.array([x[i] for i in g["sample_idx"]])
     assert np.abs(xs - np.array(g["x_samples"])).max() <= 1e-9 * g["x_absmax"]
     assert abs(x.sum() - g["x_sum"]) <= 1e-9 * g["x_absmax"] * x.size
+
+
+@pytest.mark.parametrize("lin", ["ad", "fd"])
+@pytest.mark.parametrize("c_lin", [1.0, 0.0])
+def test_conjugate_gradients_fp64(J, ctx, lin, c_lin):
+    """CG on the symmetric positive definite implicit-step Jacobians: Allen-Cahn (c = 1) and the paper's
+    reaction-diffusion sink form (c = 0), against the oracle's CG."""
+    n = 72
+    u0 = si.allen_cahn_ic(n, n, 3)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5, linear_coef=c_lin)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, c_lin))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_FP64, lin, "cg", max_krylov=500), u0, 2)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 2, _oopts(lin, "cg", max_krylov=500))
+    _compare(x, x_ref, rep, reps, 1e-10)
+    assert rep.jvp_calls == rep.krylov_its
+
+
+def test_conjugate_gradients_reduced_precision_and_options(J, ctx):
+    n = 72
+    u0 = si.allen_cahn_ic(n, n, 5)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_MIXED_FP32, "ad", "cg", tol_n=1e-9, tol_k=1e-5, max_newton=30,
+                                       max_krylov=500), u0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts("ad", "gmres", 40, 1e-12, 1e-12))
+    assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5
+    assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-9 * reps[0].res0 * 1.0001
+    xt = torch.tensor(u0, device="cuda")
+    assert J.jfnk_solve(ctx, _opts(J, J.JFNK_MIXED_BF16, "ad", "cg"), None, xt, 1, None) == J.JFNK_E_INVALID
