@@ -66,6 +66,10 @@ def _args():
     ap.add_argument("--no-cpu", action="store_true", help="skip the CPU oracle sample")
     ap.add_argument("--no-serve", action="store_true", help="skip the served request stream")
     ap.add_argument("--serve-requests", type=int, default=24)
+    ap.add_argument("--configs", action="store_true",
+                    help="instead of the timed benchmark: Newton/Krylov counts and completion per configuration, "
+                         "AD vs FD, one JSON line")
+    ap.add_argument("--config-seeds", type=int, default=32, help="Allen-Cahn seeds for the completion rate")
     return ap.parse_args()
 
 
@@ -274,6 +278,101 @@ def served_stream(J, device: int, n_req: int) -> dict:
             "stream": "Poisson 40/s, Allen-Cahn + radiation, grids 64..512, 1..4 steps, precision mixed|fp64"}
 
 
+def config_sweep(a) -> None:
+    """Newton/Krylov counts and completion per benchmark configuration, AD against FD.
+
+    A run completes when every implicit step (or the nonlinear solve) ends with the Newton test met
+    (status OK). Counts are per Newton step (Krylov) and per implicit step (Newton).
+    """
+    import torch
+    import synthetic_inputs as si
+    from paper_2605_13378_gb300 import jfnk as J
+    torch.cuda.set_device(0)
+    ctx = J.jfnk_create(0)
+    out = {"mode": "configs", "data": "synthetic", "results": []}
+
+    def opts(prec, lin, krylov="gmres", restart=40, tol_n=None, tol_k=None, max_newton=15, max_krylov=100,
+             ortho="cgs2"):
+        o = J.jfnk_default_opts(prec)
+        o.lin = J.JFNK_AD if lin == "ad" else J.JFNK_FD
+        o.krylov = J.JFNK_GMRES if krylov == "gmres" else J.JFNK_BICGSTAB
+        o.restart, o.max_newton, o.max_krylov = restart, max_newton, max_krylov
+        if tol_n is not None:
+            o.tol_newton = tol_n
+        if tol_k is not None:
+            o.tol_krylov = tol_k
+        o.ortho = J.JFNK_DCGS2 if ortho == "dcgs2" else J.JFNK_CGS2
+        return o
+
+    def summary(name, reps, sts, steps, t):
+        done = [r for r, s in zip(reps, sts) if s == J.JFNK_OK and r.steps_failed == 0]
+        newton = sum(r.newton_its for r in reps)
+        krylov = sum(r.krylov_its for r in reps)
+        return {"config": name, "runs": len(reps), "completed": len(done), "completion": len(done) / len(reps),
+                "newton_per_step": newton / max(1, steps * len(reps)), "krylov_per_newton": krylov / max(1, newton),
+                "ls_backtracks": sum(r.ls_backtracks for r in reps), "krylov_failures": sum(r.krylov_failures for r in reps),
+                "statuses": sorted({J.jfnk_status_string(s) for s in sts}), "seconds": round(t, 3)}
+
+    def solve_one(lp, o, x0, steps):
+        J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+        x = torch.tensor(x0, device="cuda")
+        rep = J.jfnk_report()
+        s = J.jfnk_solve(ctx, o, None, x, steps, rep)
+        return rep, s
+
+    # 1D Burgers, one backward-Euler step, FP64, GMRES(30), tol 1e-10
+    lp = J.make_problem("burgers1d", 1024, 1, 1e-3, 1.0, (1e-2,))
+    for lin in ("ad", "fd"):
+        t0 = time.perf_counter()
+        rep, s = solve_one(lp, opts(J.JFNK_FP64, lin, restart=30, tol_n=1e-10, tol_k=1e-10), si.burgers_ic(1024, 0), 1)
+        out["results"].append(summary(f"burgers 1024 fp64 gmres(30) {lin}", [rep], [s], 1, time.perf_counter() - t0))
+    # Allen-Cahn 512^2, 10 steps, seeds 0..S-1: {FP64, FP32} x {AD, FD} x {GMRES(40), BiCGSTAB}
+    n, steps = 512, 10
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    seeds = list(range(a.config_seeds))
+    for prec_name, prec in (("fp64", J.JFNK_FP64), ("fp32", J.JFNK_FP32)):
+        for lin in ("ad", "fd"):
+            for kr in ("gmres", "bicgstab"):
+                o = opts(prec, lin, kr)
+                t0 = time.perf_counter()
+                if kr == "gmres":     # all seeds in one batched call
+                    xs = [torch.tensor(si.allen_cahn_ic(n, n, sd), device="cuda") for sd in seeds]
+                    _, reps, sts = J.jfnk_solve_batch(ctx, [lp] * len(seeds), o, None, xs, steps)
+                else:
+                    reps, sts = [], []
+                    for sd in seeds:
+                        rep, s = solve_one(lp, o, si.allen_cahn_ic(n, n, sd), steps)
+                        reps.append(rep)
+                        sts.append(s)
+                torch.cuda.synchronize()
+                out["results"].append(summary(f"allen_cahn 512^2 x{steps} steps {prec_name} {kr} {lin}", reps, sts,
+                                              steps, time.perf_counter() - t0))
+    # radiation 1024^2, dt in {1e-3, 1e-1}, mixed, GMRES(30), one step
+    n = 1024
+    for dt in (1e-3, 1e-1):
+        lp = J.make_problem("su_olson", n, n, dt, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
+        for lin in ("ad", "fd"):
+            t0 = time.perf_counter()
+            rep, s = solve_one(lp, opts(J.JFNK_MIXED_FP32, lin, restart=30, tol_n=1e-8, tol_k=1e-6, max_krylov=30,
+                                        ortho="dcgs2"), si.su_olson_ic(n, n), 1)
+            out["results"].append(summary(f"radiation 1024^2 dt={dt:g} mixed gmres(30) {lin}", [rep], [s], 1,
+                                          time.perf_counter() - t0))
+    # Maxwell 1024^2 at ten points per wavelength, chi3 in {1e-3, 1e-1}, GMRES(60) with an FP32 basis,
+    # Born start, no preconditioner: bounded (the configuration needs the paper's preconditioner)
+    k = si.maxwell_wavenumber(n)
+    eps, f = si.maxwell_medium(n, n, 0), si.maxwell_point_source(n, n)
+    for chi in (1e-3, 1e-1):
+        lp = J.make_problem("maxwell", n, n, 0.0, 1.0, (k, chi), eps_r=eps, source=f)
+        for lin in ("ad", "fd"):
+            t0 = time.perf_counter()
+            rep, s = solve_one(lp, opts(J.JFNK_MIXED_FP32, lin, restart=60, tol_n=1e-8, tol_k=1e-6, max_newton=3,
+                                        max_krylov=10, ortho="dcgs2"), np.zeros(2 * n * n), 1)
+            out["results"].append(summary(f"maxwell 1024^2 k={k:.0f} chi3={chi:g} mixed gmres(60) {lin}", [rep], [s],
+                                          1, time.perf_counter() - t0))
+    J.jfnk_destroy(ctx)
+    print(json.dumps(out))
+
+
 def run_reference(a) -> None:
     """The oracle as it stands on this host's cores, one bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -305,6 +404,9 @@ def main() -> None:
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.configs:
+        config_sweep(a)
         return
     import torch
 
