@@ -28,6 +28,7 @@ import numpy as np
 
 from . import jvp as _jvp
 from . import krylov as _kr
+from . import pdes as _pdes
 
 
 @dataclass
@@ -44,6 +45,8 @@ class Options:
     fd_eps: float = 0.0        # > 0: fixed step, overrides the rule
     ls_c1: float = 1e-4
     ls_min_alpha: float = 2.0 ** -10
+    precond: str = "none"      # GMRES right preconditioner: "none" | "cslp" (Maxwell, App. A)
+    precond_damping: float = 0.5
 
 
 @dataclass
@@ -82,6 +85,26 @@ def _operator(problem, b, x, Fx, opt: Options, rep: Report):
     return A
 
 
+def _right_preconditioned(problem, x, A, opt: Options):
+    """(operator v -> J M^-1 v, map y -> M^-1 y) of the right preconditioner at x, or (A, None)."""
+    if opt.precond == "none":
+        return A, None
+    if opt.precond != "cslp":
+        raise ValueError(opt.precond)
+    minv = 1.0 / problem.cslp_diag(x, opt.precond_damping)
+    P = lambda y: _pdes.apply_cell_complex(minv, y)
+    return (lambda v: A(P(v))), P
+
+
+def _solve_step(problem, x, A, rhs, opt: Options):
+    """Krylov solve of J d = rhs, right-preconditioned when opt.precond says so: d = M^-1 y, J M^-1 y = rhs."""
+    Ap, P = _right_preconditioned(problem, x, A, opt)
+    kr = _krylov(Ap, rhs, opt)
+    if P is not None:
+        kr.x = P(kr.x)
+    return kr
+
+
 def _krylov(A, rhs, opt: Options):
     if opt.krylov == "gmres":
         if opt.ortho == "dcgs2":
@@ -114,7 +137,7 @@ def newton(problem, b, x0: np.ndarray, opt: Options, denom: float | None = None)
             rep.status = "max_newton"
             break
         A = _operator(problem, b, x, F, opt, rep)
-        kr = _krylov(A, -F, opt)
+        kr = _solve_step(problem, x, A, -F, opt)
         rep.krylov_its += kr.iterations
         if kr.breakdown:
             rep.status = "breakdown"
@@ -165,7 +188,7 @@ def born_start(problem, opt: Options):
     F0 = lin.residual(x0, None)
     rep = Report(res0=float(np.linalg.norm(F0)))
     A = _operator(lin, None, x0, F0, opt, rep)
-    kr = _krylov(A, -F0, opt)
+    kr = _solve_step(lin, x0, A, -F0, opt)
     rep.krylov_its = kr.iterations
     rep.status = "converged" if kr.converged else ("breakdown" if kr.breakdown else "max_newton")
     rep.res_final = float(np.linalg.norm(lin.residual(kr.x, None)))

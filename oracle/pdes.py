@@ -255,6 +255,28 @@ class MaxwellTE2D(_ThetaProblem):
         Gi = lap(B, A, +1.0) + coef * B - src[n:].reshape(ny, nx)
         return np.concatenate([Gr.reshape(-1), Gi.reshape(-1)])
 
+    def cslp_diag(self, x, damping: float = 0.5):
+        """Diagonal complex-shifted-Laplacian preconditioner at the field x (App. A, Preconditioning).
+
+        Per cell, the diagonal of the operator lap + k^2 eps with the local permittivity
+        eps(E) = eps_r + chi3 |E|^2 damped by the factor (1 - damping i):
+          M = -(2/hx^2 + 2/hy^2) + k^2 eps(E) (1 - damping i)   (complex, one per cell).
+        The absorbing walls are not part of it (the paper's form). Returns M (complex, nx*ny).
+        """
+        n = self.nx * self.ny
+        A, B = x[:n], x[n:]
+        eps = self.eps_r if self.eps_r is not None else np.ones(n)
+        hx, hy = 1.0 / self.nx, 1.0 / self.ny
+        eps_e = eps + self.chi3 * (A * A + B * B)
+        return -(2.0 / (hx * hx) + 2.0 / (hy * hy)) + self.k * self.k * eps_e * (1.0 - damping * 1j)
+
+
+def apply_cell_complex(c, v):
+    """(Re, Im) planes of v multiplied cell by cell by the complex array c."""
+    n = c.size
+    z = c * (v[:n] + 1j * v[n:])
+    return np.concatenate([z.real, z.imag])
+
 
 def make(pde: str, **kw):
     """Construct a problem by name: burgers1d, allen_cahn, su_olson, maxwell."""

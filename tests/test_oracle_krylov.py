@@ -188,3 +188,46 @@ def test_dcgs2_newton_step_equals_cgs2():
     assert [r.newton_its for r in r1] == [r.newton_its for r in r2]
     assert abs(sum(r.krylov_its for r in r1) - sum(r.krylov_its for r in r2)) <= 1
     assert np.abs(x1 - x2).max() <= 1e-12 * np.abs(x1).max()
+
+
+# ---------------------------------------------------------------------------
+# diagonal complex-shifted-Laplacian preconditioner of the Maxwell problem
+# ---------------------------------------------------------------------------
+def test_cslp_diagonal_is_the_shifted_operator_diagonal():
+    """Undamped and at chi3 = 0 the preconditioner is the diagonal of the dense (complex-step) Jacobian at
+    interior cells (the walls add the absorbing ghost, which the paper's form leaves out); damping shifts it
+    by -i d k^2 eps."""
+    import synthetic_inputs as si
+    n = 8
+    p = pdes.MaxwellTE2D(nx=n, ny=n, k=4.0, chi3=0.0, eps_r=si.maxwell_medium(n, n, 1),
+                         f=si.maxwell_point_source(n, n))
+    x = np.random.default_rng(2).standard_normal(2 * n * n)
+    Jd = jvp.dense_jacobian(lambda z: p.residual(z, None), x)
+    m0 = p.cslp_diag(x, 0.0)
+    nc = n * n
+    for j in range(1, n - 1):
+        for i in range(1, n - 1):
+            c = j * n + i
+            assert Jd[c, c] == pytest.approx(m0[c].real, rel=1e-12)
+            assert Jd[nc + c, nc + c] == pytest.approx(m0[c].real, rel=1e-12)
+            assert abs(Jd[c, nc + c]) <= 1e-12 * abs(m0[c].real)
+    m5 = p.cslp_diag(x, 0.5)
+    assert np.allclose(m5, m0 - 0.5j * p.k ** 2 * p.eps_r, rtol=1e-14, atol=0)
+    v = np.random.default_rng(3).standard_normal(2 * nc)
+    assert np.allclose(pdes.apply_cell_complex(1.0 / m5, pdes.apply_cell_complex(m5, v)), v, rtol=1e-12, atol=1e-14)
+
+
+def test_right_preconditioning_solves_the_same_system():
+    """Newton on the linear (chi3 = 0) problem with full GMRES, with and without the preconditioner: both reach
+    the dense solve of J x = f in one step."""
+    import synthetic_inputs as si
+    from oracle import newton
+    n = 6
+    p = pdes.MaxwellTE2D(nx=n, ny=n, k=3.0, chi3=0.0, eps_r=si.maxwell_medium(n, n, 0),
+                         f=si.maxwell_point_source(n, n))
+    Jd = jvp.dense_jacobian(lambda z: p.residual(z, None), np.zeros(2 * n * n))
+    x_ref = np.linalg.solve(Jd, -p.residual(np.zeros(2 * n * n), None))
+    for pc in ("none", "cslp"):
+        o = newton.Options(restart=2 * n * n, tol_newton=1e-10, tol_krylov=1e-13, max_cycles=1, precond=pc)
+        x, rep, _ = newton.bvp_solve(p, o)
+        assert np.abs(x - x_ref).max() <= 1e-9 * np.abs(x_ref).max(), pc
