@@ -238,85 +238,95 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
     if (lane == 0) s_st = v;
   }
   __syncthreads();
-  if (threadIdx.x == 0) {
-    const double alpha = sigma * sigma * S[2 * j];
-    const double rho2 = alpha - s_s2;
-    const double rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
-    s_rho = rho;
-    int active = active0;
-    int go = 1;
-    if (!finite_d(rho2) || !finite_d(sigma)) {
-      c->nonfinite = 1;
-      active = 0;
-      go = 0;
-    } else if (j == 0) {
-      c->g[0] = g_prev * rho;      // r = beta rho q_0
-    } else {
-      // complete column j-1 (kept unrotated in Hraw) and rotate it
-      const double hn = rho * isig;
+  // every thread: rho, and the completed (unrotated) column j-1 into hs
+  const double alpha = sigma * sigma * S[2 * j];
+  const double rho2 = alpha - s_s2;
+  const double rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
+  const bool bad = !finite_d(rho2) || !finite_d(sigma);
+  const double hn = rho * isig;
+  if (j > 0 && !bad) {
+    for (int i = threadIdx.x; i < j; i += blockDim.x) hs[(size_t)cj * LD + i] = col[i];
+    if (threadIdx.x == 0) {
+      hs[(size_t)cj * LD + j] = hn;
       col[j] = hn;
-      for (int i = 0; i <= j; ++i) hs[(size_t)cj * LD + i] = col[i];
-      double a = col[0];
-      for (int i = 0; i < cj; ++i) {
-        const double b = col[i + 1];
-        col[i] = s_cs[i] * a + s_sn[i] * b;
-        a = -s_sn[i] * a + s_cs[i] * b;
-      }
-      const double f = a, gg = col[cj + 1];
-      const double r = hypot(f, gg);
-      double cs = 1.0, sn = 0.0;
-      if (r != 0.0) { const double ir = 1.0 / r; cs = f * ir; sn = gg * ir; }
-      c->cs[cj] = cs;
-      c->sn[cj] = sn;
-      col[cj] = cs * f + sn * gg;
-      col[cj + 1] = 0.0;
-      const double g1 = -sn * g_prev;
-      c->g[cj + 1] = g1;
-      c->g[cj] = cs * g_prev;
-      c->k = j;
-      c->its += 1;
-      const double res = fabs(g1);
-      c->resid = res;
-      if (!finite_d(res) || !finite_d(hn)) {
+    }
+  }
+  __syncthreads();
+  if (warp == 0) {
+    // rotation of column j-1, the residual estimate and the cycle's flags; the
+    // other warps meanwhile form z, which needs only the unrotated columns
+    if (lane == 0) {
+      int active = active0;
+      int go = 1;
+      if (bad) {
         c->nonfinite = 1;
         active = 0;
-      } else if (res <= target) {
-        c->converged = 1;
-        active = 0;
-      } else if (hn == 0.0 || j >= m) {   // lucky breakdown, or the end of the cycle
-        active = 0;
+        go = 0;
+      } else if (j == 0) {
+        c->g[0] = g_prev * rho;      // r = beta rho q_0
+      } else {
+        double a = col[0];           // one dependent FMA per rotation on the carried entry
+        for (int i = 0; i < cj; ++i) {
+          const double b = col[i + 1];
+          const double cb = s_cs[i] * b, sb = s_sn[i] * b;
+          col[i] = fma(s_cs[i], a, sb);
+          a = fma(-s_sn[i], a, cb);
+        }
+        const double f = a, gg = col[cj + 1];
+        const double r = sqrt(f * f + gg * gg);   // Hessenberg entries: no overflow in the squares
+        double cs = 1.0, sn = 0.0;
+        if (r != 0.0) { const double ir = 1.0 / r; cs = f * ir; sn = gg * ir; }
+        c->cs[cj] = cs;
+        c->sn[cj] = sn;
+        col[cj] = cs * f + sn * gg;
+        col[cj + 1] = 0.0;
+        const double g1 = -sn * g_prev;
+        c->g[cj + 1] = g1;
+        c->g[cj] = cs * g_prev;
+        c->k = j;
+        c->its += 1;
+        const double res = fabs(g1);
+        c->resid = res;
+        if (!finite_d(res) || !finite_d(hn)) {
+          c->nonfinite = 1;
+          active = 0;
+        } else if (res <= target) {
+          c->converged = 1;
+          active = 0;
+        } else if (hn == 0.0 || j >= m) {   // lucky breakdown, or the end of the cycle
+          active = 0;
+        }
+        if (!active) go = 0;
       }
-      if (!active) go = 0;
+      if (go && has_w && rho == 0.0 && active) {   // the candidate vanished: nothing left to project
+        active = 0;
+        go = 0;
+      }
+      if (!has_w) go = 0;
+      if (!active) {
+        c->active = 0;
+        mirror_active(c->host_active, 0);
+      }
+      s_go = go;
     }
-    if (go && has_w && rho == 0.0 && active) {   // the candidate vanished: nothing left to project
-      active = 0;
-      go = 0;
+  } else if (!bad && has_w && rho != 0.0) {
+    // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg: warp per row
+    for (int i = warp - 1; i <= j; i += nw - 1) {
+      double z = 0.0;
+      for (int l = (i > 0 ? i - 1 : 0) + lane; l < j; l += 32) z += hs[(size_t)l * LD + i] * ss[l];
+      z = warp_sum(z);
+      if (lane == 0) zz[i] = z;
     }
-    if (!has_w) go = 0;
-    if (!active) {
-      c->active = 0;
-      mirror_active(c->host_active, 0);
-    }
-    s_go = go;
   }
   __syncthreads();
   // the completed column j-1 (unrotated and rotated) back to global memory
-  if (j > 0)
+  if (j > 0 && !bad)
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
       c->Hraw[(size_t)cj * LD + i] = hs[(size_t)cj * LD + i];
       c->H[(size_t)cj * LD + i] = col[i];
     }
   if (!s_go) return;
-  const double rho = s_rho;
   const double irho = 1.0 / rho;
-  // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg: warp per row
-  for (int i = warp; i <= j; i += nw) {
-    double z = 0.0;
-    for (int l = (i > 0 ? i - 1 : 0) + lane; l < j; l += 32) z += hs[(size_t)l * LD + i] * ss[l];
-    z = warp_sum(z);
-    if (lane == 0) zz[i] = z;
-  }
-  __syncthreads();
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
     const double h = (S[2 * i + 1] - zz[i]) * irho;
     c->hprev[i] = h;
