@@ -1,4 +1,4 @@
-"""Discrete residuals of the four benchmark PDEs (oracle; test infrastructure).
+"""Discrete residuals of the benchmark PDEs (oracle; test infrastructure).
 
 Each problem maps a flat state x (field-major, then row-major y, x) to the
 spatial operator G(x). Every function works unchanged on complex arrays so
@@ -80,6 +80,71 @@ class Burgers1D(_ThetaProblem):
         phi_p = np.where(face_speed >= 0.0, 0.5 * u * u, 0.5 * up * up)  # Phi_{i+1/2}
         phi_m = np.roll(phi_p, 1)                                        # Phi_{i-1/2}
         return -(phi_p - phi_m) / h + self.nu * (up - 2.0 * u + um) / (h * h)
+
+
+def _dc_periodic(u: np.ndarray, h: float, axis: int) -> np.ndarray:
+    """Second-order central first difference (u_{i+1} - u_{i-1}) / 2h with periodic wrap."""
+    return (np.roll(u, -1, axis=axis) - np.roll(u, 1, axis=axis)) / (2.0 * h)
+
+
+@dataclass
+class Burgers2D(_ThetaProblem):
+    """2D viscous Burgers U_t + (U . grad) U = nu lap U, U = (u, v), on the periodic square [0, L)^2.
+
+    App. A, Burgers' Equation: the advection Adv(U) = u D_x U + v D_y U with
+    second-order central first differences and the diffusion Lap(U) with the
+    5-point Laplacian, both on nodes x_i = i hx, y_j = j hy (hx = L/nx,
+    hy = L/ny). With theta = 1/2 the residual F = U - theta dt G(U) - b,
+    G = -Adv + nu Lap, is the paper's Crank-Nicolson residual of that passage.
+
+    ``courant`` > 0 makes dt adaptive: before each implicit step the time step
+    is set from the state x^n by the CFL rule of the same passage,
+        dt = C min(hx / max|u|, hy / max|v|, 1 / (2 nu (1/hx^2 + 1/hy^2))),
+    a term with max|.| = 0 dropped (``cfl_dt``). ``courant`` = 0 keeps dt.
+    """
+
+    nx: int = 64
+    ny: int = 64
+    nu: float = 0.05
+    dt: float = 1e-2
+    theta: float = 0.5
+    L: float = 2.0 * np.pi
+    courant: float = 0.0
+
+    @property
+    def n_unknowns(self) -> int:
+        return 2 * self.nx * self.ny
+
+    @property
+    def spacing(self):
+        return self.L / self.nx, self.L / self.ny
+
+    def G(self, x):
+        n = self.nx * self.ny
+        u = x[:n].reshape(self.ny, self.nx)
+        v = x[n:].reshape(self.ny, self.nx)
+        hx, hy = self.spacing
+        out = []
+        for w in (u, v):
+            adv = u * _dc_periodic(w, hx, 1) + v * _dc_periodic(w, hy, 0)
+            out.append((-adv + self.nu * _lap5_periodic(w, hx, hy)).reshape(-1))
+        return np.concatenate(out)
+
+    def cfl_dt(self, x) -> float:
+        n = self.nx * self.ny
+        hx, hy = self.spacing
+        cands = [1.0 / (2.0 * self.nu * (1.0 / hx ** 2 + 1.0 / hy ** 2))] if self.nu > 0 else []
+        umax, vmax = float(np.abs(x[:n]).max()), float(np.abs(x[n:]).max())
+        if umax > 0.0:
+            cands.append(hx / umax)
+        if vmax > 0.0:
+            cands.append(hy / vmax)
+        return self.courant * min(cands)
+
+    def rhs(self, xn):
+        if self.courant > 0.0:
+            self.dt = self.cfl_dt(xn)
+        return super().rhs(xn)
 
 
 @dataclass
@@ -279,6 +344,6 @@ def apply_cell_complex(c, v):
 
 
 def make(pde: str, **kw):
-    """Construct a problem by name: burgers1d, allen_cahn, su_olson, maxwell."""
-    return {"burgers1d": Burgers1D, "allen_cahn": AllenCahn2D,
+    """Construct a problem by name: burgers1d, burgers2d, allen_cahn, su_olson, maxwell."""
+    return {"burgers1d": Burgers1D, "burgers2d": Burgers2D, "allen_cahn": AllenCahn2D,
             "su_olson": SuOlson2D, "maxwell": MaxwellTE2D}[pde](**kw)

@@ -33,6 +33,56 @@ def burgers_ic(N: int = 1024, seed: int = 0) -> np.ndarray:
     return np.sin(2.0 * math.pi * x) + 0.1 * eta
 
 
+BURGERS2D_KINDS = ("tgv", "dsl", "4vc")
+
+# Four-vortex collision layout: centres on the corners of a square of side
+# 2 d around the domain centre, circulations of alternating sign going
+# round it, all of the same magnitude.
+VC4_R, VC4_D, VC4_GAMMA = 0.5, 1.0, 4.0
+
+
+def burgers2d_ic(nx: int, ny: int | None = None, kind: str = "tgv", L: float = 2.0 * math.pi) -> np.ndarray:
+    """Initial velocity [u, v] (flat) of the 2D Burgers benchmarks on the periodic square [0, L)^2.
+
+    Nodes are at x_i = i L / nx, y_j = j L / ny (the grid of the 2D Burgers
+    residual, unlike the cell-centred grids of the other 2D problems).
+    Formulas for L = 2 pi (App. A, Burgers' Equation):
+
+    * ``tgv``: Taylor-Green vortex u = sin x cos y, v = -cos x sin y.
+    * ``dsl``: double shear layer, rho = 30, delta = 0.05:
+      u = tanh(rho (y - pi/2)) for y <= pi, tanh(rho (3 pi/2 - y)) above;
+      v = delta sin x.
+    * ``4vc``: four Gaussian vortices of radius R = 0.5,
+      U = sum_i Gamma_i (-(y - cy_i), x - cx_i) exp(-r_i^2 / R^2), with the
+      centres (pi -+ 1, pi -+ 1) and Gamma = +4, -4, +4, -4 going round them
+      (the paper gives R and the alternating signs only).
+    """
+    ny = nx if ny is None else ny
+    x = np.arange(nx, dtype=np.float64) * (L / nx)
+    y = np.arange(ny, dtype=np.float64) * (L / ny)
+    X, Y = np.meshgrid(x, y)            # shape (ny, nx), row-major (y, x)
+    pi = math.pi
+    if kind == "tgv":
+        u, v = np.sin(X) * np.cos(Y), -np.cos(X) * np.sin(Y)
+    elif kind == "dsl":
+        rho, delta = 30.0, 0.05
+        u = np.where(Y <= pi, np.tanh(rho * (Y - pi / 2)), np.tanh(rho * (3 * pi / 2 - Y)))
+        v = delta * np.sin(X)
+    elif kind == "4vc":
+        c, d = L / 2.0, VC4_D
+        centres = ((c - d, c - d), (c + d, c - d), (c + d, c + d), (c - d, c + d))
+        u = np.zeros_like(X)
+        v = np.zeros_like(X)
+        for k, (cx, cy) in enumerate(centres):
+            g = VC4_GAMMA * (1.0 if k % 2 == 0 else -1.0)
+            ex = np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / VC4_R ** 2)
+            u += -g * (Y - cy) * ex
+            v += g * (X - cx) * ex
+    else:
+        raise ValueError(f"unknown 2D Burgers initial condition {kind!r}")
+    return np.concatenate([u.reshape(-1), v.reshape(-1)])
+
+
 def allen_cahn_ic(nx: int, ny: int | None = None, seed: int = 0) -> np.ndarray:
     """Uniform noise in [-0.1, 0.1] on an nx x ny periodic grid (flat, row-major)."""
     ny = nx if ny is None else ny

@@ -35,10 +35,13 @@ def _problems(rng):
                          f=si.maxwell_point_source(n, n + 2))
     x = rng.standard_normal(m.n_unknowns)
     out.append(("maxwell", m, x, None))
+    g = pdes.Burgers2D(nx=n, ny=n + 2, nu=0.05, dt=0.05)
+    x = rng.uniform(-1, 1, g.n_unknowns)
+    out.append(("burgers2d", g, x, g.rhs(x * 0.9)))
     return out
 
 
-@pytest.mark.parametrize("idx", range(4))
+@pytest.mark.parametrize("idx", range(5))
 def test_taylor_remainder_is_second_order(rng, idx):
     name, p, x, b = _problems(rng)[idx]
     v = rng.standard_normal(x.size)
