@@ -70,6 +70,11 @@ def _args():
                     help="instead of the timed benchmark: Newton/Krylov counts and completion per configuration, "
                          "AD vs FD, one JSON line")
     ap.add_argument("--config-seeds", type=int, default=32, help="Allen-Cahn seeds for the completion rate")
+    ap.add_argument("--suite", action="store_true",
+                    help="the paper's 2D Burgers suite (TGV, DSL, 4VC x nu x grid) over eight solver variants, "
+                         "with Dolan-More performance profiles, instead of the benchmark")
+    ap.add_argument("--suite-steps", type=int, default=10, help="implicit steps per suite run")
+    ap.add_argument("--suite-grids", default="256,512", help="grid sizes of the suite")
     return ap.parse_args()
 
 
@@ -373,6 +378,89 @@ def config_sweep(a) -> None:
     print(json.dumps(out))
 
 
+SUITE_VARIANTS = [(prec, lin, kr) for prec in ("fp64", "fp32") for lin in ("ad", "fd") for kr in ("gmres", "bicgstab")]
+PROFILE_TAUS = (1.0, 1.5, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0, 1024.0)
+
+
+def run_failed(status_ok: bool, fatal: bool, steps: int, steps_failed: int) -> bool:
+    """The paper's failure rule for a time-dependent run (Sec. 4, metrics and failure criteria): it fails when
+    it stops early (non-finite values, breakdown, a library error) or when more than 20% of its implicit steps
+    miss 100 x tol_Newton."""
+    if fatal:
+        return True
+    return steps_failed > 0.2 * steps
+
+
+def performance_profile(times: dict, taus=PROFILE_TAUS) -> dict:
+    """Dolan-More profiles: times[solver][problem] = metric, None for a failed run.
+
+    r_ps = t_ps / min_s t_ps over the solvers that completed p (a failed run has r = inf);
+    rho_s(tau) = |{p : r_ps <= tau}| / |P|. Problems no solver completed count in |P| for every solver."""
+    solvers = sorted(times)
+    problems = sorted({p for s in solvers for p in times[s]})
+    best = {}
+    for p in problems:
+        ok = [times[s][p] for s in solvers if times[s].get(p) is not None]
+        best[p] = min(ok) if ok else None
+    out = {}
+    for s in solvers:
+        r = []
+        for p in problems:
+            t = times[s].get(p)
+            r.append(math.inf if (t is None or best[p] is None) else t / best[p])
+        out[s] = {"rho": [sum(1 for x in r if x <= tau) / len(problems) for tau in taus],
+                  "completion": sum(1 for x in r if x < math.inf) / len(problems)}
+    return {"taus": list(taus), "problems": len(problems), "profiles": out}
+
+
+def burgers2d_suite(a) -> None:
+    """The paper's 2D Burgers benchmark (App. A): TGV, DSL and 4VC at nu in {0.1, 0.05, 0.01} on the GPU grids,
+    Courant number 1, Crank-Nicolson, solved by each of {FP64, FP32} x {AD, FD} x {GMRES(30), BiCGSTAB} with the
+    paper's tolerances and caps; Dolan-More profiles by wall time and by Krylov iterations."""
+    import torch
+    import synthetic_inputs as si
+    from paper_2605_13378_gb300 import jfnk as J
+    torch.cuda.set_device(0)
+    ctx = J.jfnk_create(0)
+    grids = [int(g) for g in a.suite_grids.split(",") if g]
+    steps = a.suite_steps
+    fatal_codes = {J.JFNK_E_NONFINITE, J.JFNK_E_BREAKDOWN, J.JFNK_E_CUDA, J.JFNK_E_TIMEOUT, J.JFNK_E_OOM,
+                   J.JFNK_E_INVALID}
+    runs, t_wall, t_kry = [], {}, {}
+    for n in grids:
+        for kind in si.BURGERS2D_KINDS:
+            x0 = si.burgers2d_ic(n, n, kind)
+            for nu in (0.1, 0.05, 0.01):
+                prob = f"{kind} nu={nu:g} {n}^2"
+                lp = J.make_problem("burgers2d", n, n, 0.0, 0.5, (nu, 0.0, 1.0))
+                J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+                for prec, lin, kr in SUITE_VARIANTS:
+                    o = J.jfnk_default_opts(J.JFNK_FP64 if prec == "fp64" else J.JFNK_FP32)
+                    o.lin = J.JFNK_AD if lin == "ad" else J.JFNK_FD
+                    o.krylov = J.JFNK_GMRES if kr == "gmres" else J.JFNK_BICGSTAB
+                    o.restart = 30
+                    x = torch.tensor(x0, device="cuda")
+                    rep = J.jfnk_report()
+                    torch.cuda.synchronize()
+                    t0 = time.perf_counter()
+                    s = J.jfnk_solve(ctx, o, None, x, steps, rep)
+                    torch.cuda.synchronize()
+                    dt_wall = time.perf_counter() - t0
+                    failed = run_failed(s == J.JFNK_OK, s in fatal_codes, steps, rep.steps_failed)
+                    var = f"{lin.upper()}-{prec.upper()}-{'GMRES' if kr == 'gmres' else 'BiCGSTAB'}"
+                    t_wall.setdefault(var, {})[prob] = None if failed else dt_wall
+                    t_kry.setdefault(var, {})[prob] = None if failed else max(1, rep.krylov_its)
+                    runs.append({"problem": prob, "solver": var, "status": J.jfnk_status_string(s),
+                                 "failed": failed, "seconds": round(dt_wall, 4), "steps_done": rep.steps_done,
+                                 "steps_failed": rep.steps_failed, "newton": rep.newton_its, "krylov": rep.krylov_its,
+                                 "ls_backtracks": rep.ls_backtracks, "dt_last": rep.dt_last})
+    J.jfnk_destroy(ctx)
+    out = {"mode": "suite", "pde": "burgers2d", "data": "synthetic", "steps": steps, "grids": grids,
+           "courant": 1.0, "restart": 30, "runs": runs,
+           "profile_wall_time": performance_profile(t_wall), "profile_krylov_its": performance_profile(t_kry)}
+    print(json.dumps(out))
+
+
 def run_reference(a) -> None:
     """The oracle as it stands on this host's cores, one bounded sample per step."""
     rank = int(os.environ.get("RANK", "0"))
@@ -404,6 +492,9 @@ def main() -> None:
     a = _args()
     if a.impl == "reference":
         run_reference(a)
+        return
+    if a.suite:
+        burgers2d_suite(a)
         return
     if a.configs:
         config_sweep(a)

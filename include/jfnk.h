@@ -67,9 +67,20 @@ typedef enum {
   JFNK_ALLEN_CAHN2D = 1,  /* p[0] = D, p[1] = coefficient of the +u term (1 or 0)   */
   JFNK_SU_OLSON2D = 2,    /* p[0] = sigma, p[1] = a, p[2] = T_b, p[3] = rho,
                              p[4] = 1 flux limiter on / 0 off                        */
-  JFNK_MAXWELL_TE2D = 3   /* p[0] = k, p[1] = chi3; aux[0] = eps_r (nx*ny),
+  JFNK_MAXWELL_TE2D = 3,  /* p[0] = k, p[1] = chi3; aux[0] = eps_r (nx*ny),
                              aux[1] = source (Re plane, Im plane; 2*nx*ny)           */
+  JFNK_BURGERS2D = 4      /* p[0] = nu >= 0, p[1] = side L of the periodic square
+                             (0: 2 pi), p[2] = Courant number C (0: fixed dt)       */
 } jfnk_pde;
+/* JFNK_BURGERS2D is the paper's 2D viscous Burgers problem (App. A, Burgers'
+ * Equation): U = (u, v) on nodes x_i = i L/nx, y_j = j L/ny of the periodic
+ * square, second-order central differences for the advection u D_x U +
+ * v D_y U and the 5-point Laplacian for nu lap U; state [u plane, v plane].
+ * With C > 0 each implicit step of jfnk_solve first sets its time step from
+ * the current state by the CFL rule of that passage,
+ *   dt = C min(hx / max|u|, hy / max|v|, 1 / (2 nu (1/hx^2 + 1/hy^2))),
+ * a term whose denominator is zero left out (all left out: JFNK_E_INVALID);
+ * the maxima are reduced on the device and prob.dt is ignored. */
 typedef enum {
   JFNK_FP64 = 0,        /* everything in FP64                                                 */
   JFNK_FP32 = 1,        /* state, residual, JVP and basis in FP32 (Hessenberg in FP64)        */
@@ -127,6 +138,7 @@ typedef struct {
   double res0;          /* ||F(x*)|| of the last solve (Eq. 5 denominator) */
   double res_final;     /* final ||F|| of the last solve */
   double ms;            /* host wall time of the call */
+  double dt_last;       /* time step of the last implicit step (the CFL step when adaptive) */
 } jfnk_report;
 
 /* Defaults of the paper for a precision (Sec. 3.3): tol_Newton 1e-6 / 1e-4,

@@ -17,6 +17,7 @@ cudaError_t batch_launch(int pde, int ts, int tj, const BatLaunch& L, int grid, 
     case JFNK_ALLEN_CAHN2D: return batch_launch_allen_cahn(ts, tj, L, grid, st);
     case JFNK_SU_OLSON2D: return batch_launch_su_olson(ts, tj, L, grid, st);
     case JFNK_MAXWELL_TE2D: return batch_launch_maxwell(ts, tj, L, grid, st);
+    case JFNK_BURGERS2D: return batch_launch_burgers2d(ts, tj, L, grid, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -28,6 +29,7 @@ int batch_grid_cap(int pde, int ts, int tj, int nsm) {
     case JFNK_ALLEN_CAHN2D: occ = batch_occ_allen_cahn(ts, tj); break;
     case JFNK_SU_OLSON2D: occ = batch_occ_su_olson(ts, tj); break;
     case JFNK_MAXWELL_TE2D: occ = batch_occ_maxwell(ts, tj); break;
+    case JFNK_BURGERS2D: occ = batch_occ_burgers2d(ts, tj); break;
   }
   return std::max(1, occ) * nsm;
 }
@@ -52,7 +54,7 @@ size_t carve(const jfnk_problem* pr, const jfnk_opts* o, unsigned char* base, Ba
   int ts = 0, tj = 0;
   pair_of(o->prec, &ts, &tj);
   const long long ncell = (long long)pr->nx * pr->ny;
-  const int nf = (pr->pde == JFNK_SU_OLSON2D || pr->pde == JFNK_MAXWELL_TE2D) ? 2 : 1;
+  const int nf = pde_nfields(pr->pde);
   const size_t N = (size_t)ncell * nf;
   const size_t ss = vt_size(ts), sj = vt_size(tj);
   const bool mixed = ts != tj;
@@ -217,6 +219,7 @@ jfnk_status BatchEngine::admit(const BatRequest& r, std::string* why) {
     jfnk_status s = grow(std::max(16, 2 * cap_), why);
     if (s) return s;
   }
+  if (r.prob.pde * 3 + pc >= kGroups) { if (why) *why = "no batch group for this PDE"; return JFNK_E_INVALID; }
   Slot& S = slots_[slot];
   const size_t bytes = carve(&r.prob, &r.opts, nullptr, nullptr);
   void* ws = nullptr;
@@ -374,6 +377,7 @@ jfnk_status BatchEngine::finish(int i, BatResult* out, std::string* why) {
   rep.krylov_failures = st.krylov_failures;
   rep.res0 = st.res0;
   rep.res_final = st.res_final;
+  rep.dt_last = st.dt;
   rep.ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - s.t0).count();
   out->tag = s.req.tag;
   out->status = (jfnk_status)st.first_bad;

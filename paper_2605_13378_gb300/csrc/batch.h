@@ -25,6 +25,7 @@ constexpr int kBatPart = 72;       // partial sums kept per unit (>= kMaxM + 1)
 
 enum BatPhase {
   PH_IN = 0,     // state <- caller's initial value (zero for the Born stage)
+  PH_CFL,        // adaptive time step: max|u|, max|v| -> CFL rule (2D Burgers with C > 0)
   PH_RHS,        // b = M(x^n) + (1 - theta) dt G(x^n)
   PH_RES,        // F(x), ||F||^2, ||x||^2 (and the FP32 copy of x)
   PH_FX32,       // F(x) in FP32 for the FD quotient of a mixed-precision solve
@@ -48,6 +49,7 @@ struct BatState {
   int pad_;
   double fn2, fnorm, f0, alpha, dn2, res0, res_final;
   double xn2[2];                   // ||x||^2 of the two state buffers
+  double dt, thdt, c_old;          // time step of the current implicit step, theta dt, (1 - theta) dt
   GmresCtl g;
 };
 
@@ -87,9 +89,11 @@ cudaError_t batch_launch_burgers(int ts, int tj, const BatLaunch& L, int grid, c
 cudaError_t batch_launch_allen_cahn(int ts, int tj, const BatLaunch& L, int grid, cudaStream_t st);
 cudaError_t batch_launch_su_olson(int ts, int tj, const BatLaunch& L, int grid, cudaStream_t st);
 cudaError_t batch_launch_maxwell(int ts, int tj, const BatLaunch& L, int grid, cudaStream_t st);
+cudaError_t batch_launch_burgers2d(int ts, int tj, const BatLaunch& L, int grid, cudaStream_t st);
 int batch_occ_burgers(int ts, int tj);
 int batch_occ_allen_cahn(int ts, int tj);
 int batch_occ_su_olson(int ts, int tj);
 int batch_occ_maxwell(int ts, int tj);
+int batch_occ_burgers2d(int ts, int tj);
 
 }  // namespace jfnk

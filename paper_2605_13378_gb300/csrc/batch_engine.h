@@ -74,7 +74,7 @@ class BatchEngine {
     int group = 0;
     std::chrono::steady_clock::time_point t0;
   };
-  static constexpr int kGroups = 12;    // 4 PDEs x 3 precision pairs
+  static constexpr int kGroups = 15;    // 5 PDEs (jfnk_pde) x 3 precision pairs
   jfnk_status rebuild(std::string* why);
   jfnk_status grow(int cap, std::string* why);
   jfnk_status finish(int slot, BatResult* out, std::string* why);

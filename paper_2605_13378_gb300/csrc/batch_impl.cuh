@@ -99,6 +99,28 @@ __device__ __forceinline__ void bat_unit_sum(double (&v)[K], double* dst) {
   __syncthreads();
 }
 
+// Maxima of two per-thread values over the CTA into dst[0..2).
+__device__ __forceinline__ void bat_unit_max2(double (&v)[2], double* dst) {
+  __shared__ double red[kBatThreads / 32][2];
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+  for (int k = 0; k < 2; ++k) {
+    double s = v[k];
+    for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+    if (lane == 0) red[warp][k] = s;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < 2; ++k) {
+      double s = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = fmax(s, red[w][k]);
+      dst[k] = s;
+    }
+  }
+  __syncthreads();
+}
+
 // ---------------------------------------------------------------------------
 // per-tile work of each phase
 // ---------------------------------------------------------------------------
@@ -377,9 +399,30 @@ struct BatTile {
     }
   }
 
+  // per unit: max|u|, max|v| of the state (a non-finite value counts as +Inf)
+  __device__ static void cfl_max(const BatDesc& D, const ProbDev& P, const BatState& S, int t) {
+    const long long nc = P.ncell;
+    const TS* x = (const TS*)D.x[S.cur];
+    const long long u0 = (long long)t * (D.tc / kBatUnit);
+    const long long u1 = min(u0 + D.tc / kBatUnit, (long long)D.nunit);
+    for (long long u = u0; u < u1; ++u) {
+      const long long c = u * kBatUnit + threadIdx.x;
+      double m[2] = {0.0, 0.0};
+      if (c < nc) {
+#pragma unroll
+        for (int f = 0; f < 2; ++f) {
+          const double a = fabs((double)x[f * nc + c]);
+          m[f] = a <= 1.7976931348623157e308 ? a : 1.0 / 0.0;
+        }
+      }
+      bat_unit_max2(m, D.part + u * kBatPart);
+    }
+  }
+
   __device__ static void work(const BatDesc& D, const BatState& S, int ph, int t, A* ws) {
     ProbDev P = D.P;
     if (D.born && S.stage == 0) P.p1 = 0.0;     // Born stage: the chi3 = 0 problem
+    if (P.cfl > 0.0) { P.thdt = S.thdt; P.c_old = S.c_old; }   // adaptive step of this implicit step
     const long long nc = P.ncell;
     const long long c0 = (long long)t * D.tc, c1 = min(c0 + D.tc, nc);
     switch (ph) {
@@ -392,6 +435,7 @@ struct BatTile {
             x[f * nc + c] = zero ? TS(0) : (TS)D.io[f * nc + c];
         break;
       }
+      case PH_CFL: if constexpr (PDE::NF == 2) cfl_max(D, P, S, t); break;
       case PH_RHS: rhs(D, P, S, c0, c1); break;
       case PH_RES: residual(D, P, S, t, false); break;
       case PH_LS: residual(D, P, S, t, true); break;
@@ -457,7 +501,7 @@ __device__ __forceinline__ void bat_end_solve(const BatDesc& D, BatState& S, int
   if (!ok) S.steps_failed += 1;
   if (ns == JFNK_E_NONFINITE || ns == JFNK_E_BREAKDOWN) { S.phase = PH_OUT; return; }
   S.step += 1;
-  S.phase = S.step < D.steps ? PH_RHS : PH_OUT;
+  S.phase = S.step < D.steps ? (D.P.cfl > 0.0 ? PH_CFL : PH_RHS) : PH_OUT;
 }
 
 __device__ __forceinline__ void bat_newton_test(const BatDesc& D, BatState& S) {
@@ -518,8 +562,26 @@ __device__ __forceinline__ void bat_control(const BatDesc& D, BatState& S, int p
     case PH_IN:
       S.fresh = 1;
       S.newton_it = 0;
-      S.phase = D.P.bvp ? PH_RES : PH_RHS;
+      S.dt = D.P.dt; S.thdt = D.P.thdt; S.c_old = D.P.c_old;
+      S.phase = D.P.bvp ? PH_RES : (D.P.cfl > 0.0 ? PH_CFL : PH_RHS);
       break;
+    case PH_CFL: {
+      const double dt = cfl_rule(sum[0], sum[1], D.P.hx, D.P.hy, D.P.p0, D.P.cfl);
+      S.dt = dt;
+      if (dt > 0.0 && dt <= 1.7976931348623157e308) {
+        S.thdt = D.P.theta * dt;
+        S.c_old = (1.0 - D.P.theta) * dt;
+        S.phase = PH_RHS;
+      } else {
+        // non-finite state (NaN) or an undefined rule (+Inf: nu = 0 and the state at rest)
+        const int ns = (dt == dt) ? JFNK_E_INVALID : JFNK_E_NONFINITE;
+        S.status = ns;
+        if (S.first_bad == 0) S.first_bad = ns;
+        S.steps_failed += 1;
+        S.phase = PH_OUT;
+      }
+      break;
+    }
     case PH_RHS:
       S.fresh = 1;
       S.newton_it = 0;
@@ -606,7 +668,7 @@ __device__ __forceinline__ void bat_control(const BatDesc& D, BatState& S, int p
 
 __device__ __forceinline__ int bat_nvals(const BatState& S, int ph) {
   switch (ph) {
-    case PH_RES: case PH_LS: return 2;
+    case PH_RES: case PH_LS: case PH_CFL: return 2;
     case PH_A1: case PH_A2: return S.j + 1;
     case PH_A3: case PH_GUPD: case PH_RJVP: return 1;
     default: return 0;
@@ -645,8 +707,15 @@ __global__ void __launch_bounds__(kBatThreads) k_batch(BatLaunch L) {
         const int nv = bat_nvals(S, ph);
         const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
         for (int v = warp; v < nv; v += nw) {
-          double s = lane_strided_sum(D.part + v, kBatPart, D.nunit, lane);
-          s = warp_sum(s);
+          double s;
+          if (ph == PH_CFL) {
+            s = 0.0;
+            for (int u = lane; u < D.nunit; u += 32) s = fmax(s, D.part[(size_t)u * kBatPart + v]);
+            for (int o = 16; o > 0; o >>= 1) s = fmax(s, __shfl_xor_sync(0xffffffffu, s, o));
+          } else {
+            s = lane_strided_sum(D.part + v, kBatPart, D.nunit, lane);
+            s = warp_sum(s);
+          }
           if (lane == 0) s_sum[v] = s;
         }
         __syncthreads();

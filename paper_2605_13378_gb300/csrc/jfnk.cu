@@ -32,12 +32,12 @@ namespace {
 
 enum KClass {
   KC_RESIDUAL, KC_RHS, KC_JVP_AD, KC_JVP_FD, KC_ARN1, KC_ARN2, KC_ARN3, KC_GINIT, KC_GFIN, KC_CAST,
-  KC_VDOTS, KC_BICG, KC_DCGS1, KC_DCGS2, KC_COUNT
+  KC_VDOTS, KC_BICG, KC_DCGS1, KC_DCGS2, KC_CFL, KC_COUNT
 };
 const char* kKClassNames[KC_COUNT] = {
     "residual", "rhs", "jvp_ad", "jvp_fd", "arnoldi_dots", "arnoldi_update_dots", "arnoldi_update_norm_givens",
     "gmres_init", "gmres_backsolve_update", "cast", "vdots", "bicgstab_vector", "arnoldi_dcgs_dots",
-    "arnoldi_dcgs_update"};
+    "arnoldi_dcgs_update", "cfl_dt"};
 
 constexpr int kLookahead = 3;   // Arnoldi / BiCGSTAB steps the host may run ahead of the device
 
@@ -317,6 +317,21 @@ struct Solver {
   jfnk_status sync_read(const void* dev, size_t bytes) {
     CK(cudaMemcpyAsync(ctx->hbuf, dev, bytes, cudaMemcpyDeviceToHost, ctx->stream), "read-back");
     CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+    return JFNK_OK;
+  }
+
+  // ---- adaptive time step (2D Burgers CFL rule) from the current state x;
+  // *dt gets the step (NaN when the state is not finite) -----------------
+  jfnk_status cfl_step(double* dt) {
+    const int ev = tm_begin(ctx, KC_CFL, (double)N * vt_size(ts), -1);
+    cudaError_t e = launch_cfl_dt(P, ts, x, ctx->dsc + 16, ctx->red, ctx->nsm, ctx->stream);
+    tm_end(ctx, ev);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "cfl kernel");
+    jfnk_status s = sync_read(ctx->dsc + 16, sizeof(double));
+    if (s) return s;
+    *dt = ctx->hbuf[0];
+    if (std::isinf(*dt)) return fail(ctx, JFNK_E_INVALID, "CFL step undefined: nu = 0 and the state is at rest");
+    if (std::isfinite(*dt)) set_dt(&P, *dt);
     return JFNK_OK;
   }
 
@@ -664,7 +679,7 @@ namespace jfnk {
 size_t workspace_estimate(const jfnk_problem* pr, const jfnk_opts* o) {
   int ts, tj, tb;
   if (!pr || !o || !prec_types(o->prec, &ts, &tj, &tb) || pr->nx < 1 || pr->ny < 1) return 0;
-  const size_t nf = (pr->pde == JFNK_SU_OLSON2D || pr->pde == JFNK_MAXWELL_TE2D) ? 2 : 1;
+  const size_t nf = (size_t)pde_nfields(pr->pde);
   const size_t N = (size_t)pr->nx * pr->ny * nf;
   const size_t ss = vt_size(ts), sj = vt_size(tj), sb = vt_size(tb);
   size_t b = N * (7 * ss + 8 + 3 * sj) + (tj != ts ? 4 * N * sj : 0);
@@ -974,6 +989,19 @@ jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_pre
     if (!(sv.rep.res0 == 0.0 || sv.rep.res_final / sv.rep.res0 < 100.0 * opts->tol_newton)) sv.rep.steps_failed = 1;
   } else {
     for (int step = 0; step < steps; ++step) {
+      sv.rep.dt_last = ctx->prob.dt;
+      if (sv.P.cfl > 0.0) {
+        double dt = 0.0;
+        s = sv.cfl_step(&dt);
+        if (s) return s;
+        sv.rep.dt_last = dt;
+        if (!std::isfinite(dt)) {
+          sv.rep.status = JFNK_E_NONFINITE;
+          sv.rep.steps_failed += 1;
+          if (first_bad == JFNK_OK) first_bad = JFNK_E_NONFINITE;
+          break;
+        }
+      }
       // x^n -> b_n; x starts from x^n
       const int evr = tm_begin(ctx, KC_RHS, (double)N * 2 * vt_size(sv.ts), -1);
       cudaError_t e = launch_rhs(sv.P, sv.ts, sv.x, w.b, ctx->stream);

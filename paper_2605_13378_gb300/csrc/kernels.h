@@ -16,6 +16,10 @@ namespace jfnk {
 
 enum VType { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2 };
 inline size_t vt_size(int t) { return t == VT_F64 ? 8 : (t == VT_F32 ? 4 : 2); }
+// Fields per cell of a PDE (jfnk_pde).
+inline int pde_nfields(int pde) {
+  return (pde == JFNK_SU_OLSON2D || pde == JFNK_MAXWELL_TE2D || pde == JFNK_BURGERS2D) ? 2 : 1;
+}
 
 // Device workspace of one reduction site (partials + arrival counter).
 struct RedWs {
@@ -77,5 +81,13 @@ struct JvpArgs {
   const int* active;           // device flag: the kernel does nothing when *active == 0 (null: always run)
 };
 cudaError_t launch_jvp(const ProbDev& P, const JvpArgs& a, RedWs red, cudaStream_t st);
+
+// Adaptive time step of the 2D Burgers problem from the state x (precision
+// t, fields u and v): *dt_out = C min(hx / max|u|, hy / max|v|,
+// 1 / (2 nu (1/hx^2 + 1/hy^2))), terms with a zero denominator left out
+// (none left: +Inf); NaN when x holds a non-finite value. Grid: at most
+// 4 nsm blocks of 256 threads, partials in red.
+cudaError_t launch_cfl_dt(const ProbDev& P, int t, const void* x, double* dt_out, RedWs red, int nsm,
+                          cudaStream_t st);
 
 }  // namespace jfnk

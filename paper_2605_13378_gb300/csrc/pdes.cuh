@@ -1,4 +1,4 @@
-// pdes.cuh -- per-cell discrete residuals of the four benchmark PDEs.
+// pdes.cuh -- per-cell discrete residuals of the benchmark PDEs.
 //
 // Each PDE is a struct with a static `cell` function that, given the values
 // of the 3 x 3 neighbourhood of cell (i, j) for every field, returns per
@@ -27,6 +27,10 @@ struct ProbDev {
   long long ncell;        // nx * ny
   double thdt;            // theta * dt (unused by the boundary-value problem)
   double c_old;           // (1 - theta) * dt
+  double dt;              // time step installed by set_dt
+  double theta;           // theta of the time scheme (0 for the boundary-value problem)
+  double cfl;             // Courant number of an adaptive step (0: fixed dt)
+  double hx, hy;          // grid spacing
   double invhx, invhy, invhx2, invhy2;
   double p0, p1, p2, p3;  // PDE parameters (see jfnk_pde)
   int flag;               // Su-Olson: flux limiter on
@@ -38,6 +42,27 @@ struct ProbDev {
   const double* eps64; const float* eps32;   // eps_r plane or null (= 1)
   const double* src64; const float* src32;   // source planes (Re, Im) or null
 };
+
+// Install the time step dt of an implicit step (theta method).
+inline void set_dt(ProbDev* P, double dt) {
+  if (P->bvp) return;
+  P->dt = dt;
+  P->thdt = P->theta * dt;
+  P->c_old = (1.0 - P->theta) * dt;
+}
+
+// CFL rule of the 2D Burgers problem from umax = max|u|, vmax = max|v| (App. A,
+// Burgers' Equation): C min(hx / umax, hy / vmax, 1 / (2 nu (1/hx^2 + 1/hy^2))),
+// a term with a zero denominator left out (none left: +Inf); NaN when a
+// maximum is not finite.
+__host__ __device__ inline double cfl_rule(double umax, double vmax, double hx, double hy, double nu, double C) {
+  if (!(umax <= 1.7976931348623157e308) || !(vmax <= 1.7976931348623157e308)) return 0.0 / 0.0;
+  double dt = 1.0 / 0.0;
+  if (nu > 0.0) dt = 1.0 / (2.0 * nu * (1.0 / (hx * hx) + 1.0 / (hy * hy)));
+  if (umax > 0.0) dt = fmin(dt, hx / umax);
+  if (vmax > 0.0) dt = fmin(dt, hy / vmax);
+  return C * dt;
+}
 
 template <class T> __device__ __forceinline__ const T* eps_of(const ProbDev& P);
 template <> __device__ __forceinline__ const double* eps_of<double>(const ProbDev& P) { return P.eps64; }
@@ -82,6 +107,36 @@ struct Burgers1D {
     V phim = (primal(um) + primal(u) >= T(0)) ? half * um * um : half * u * u;
     M[0] = u;
     G[0] = (phim - phip) * T(P.invhx) + T(P.p0) * ((up - T(2) * u + um) * T(P.invhx2));
+  }
+};
+
+// ---------------------------------------------------------------------------
+// 2D viscous Burgers U_t + (U . grad) U = nu lap U, U = (u, v), periodic
+// square of side L on nodes x_i = i hx, y_j = j hy (App. A, Burgers'
+// Equation). Second-order central differences for the advection and the
+// 5-point Laplacian for the diffusion, per field w in {u, v}:
+//   G_w = nu lap w - (u (w_e - w_w) / 2hx + v (w_n - w_s) / 2hy)
+// invhx, invhy are 1/hx, 1/hy of the square (not of the unit square).
+// ---------------------------------------------------------------------------
+struct Burgers2D {
+  static constexpr int NF = 2;
+  static constexpr bool DIAG = false;
+  static constexpr int POLICY = BP_WRAP;
+  static constexpr bool AUX = false;
+  template <class T, class V>
+  __device__ __forceinline__ static void cell(const ProbDev& P, int, int, const Nb<V, 2>& q, const CellAux<T>&,
+                                              V* M, V* G) {
+    const V u = q.c[0], v = q.c[1];
+    const T hix = T(0.5) * T(P.invhx), hiy = T(0.5) * T(P.invhy);
+    const T ihx2 = T(P.invhx2), ihy2 = T(P.invhy2), nu = T(P.p0);
+#pragma unroll
+    for (int f = 0; f < 2; ++f) {
+      const V w = q.c[f];
+      V lap = (q.e[f] - T(2) * w + q.w[f]) * ihx2 + (q.n[f] - T(2) * w + q.s[f]) * ihy2;
+      V adv = u * ((q.e[f] - q.w[f]) * hix) + v * ((q.n[f] - q.s[f]) * hiy);
+      M[f] = w;
+      G[f] = nu * lap - adv;
+    }
   }
 };
 

@@ -12,7 +12,7 @@ namespace jfnk {
 bool make_probdev(const jfnk_problem* pr, ProbDev* P, std::string* why) {
   auto no = [&](const char* m) { if (why) *why = m; return false; };
   const int pde = pr->pde;
-  if (pde < 0 || pde > 3) return no("unknown pde");
+  if (pde < 0 || pde > 4) return no("unknown pde");
   if (pde == JFNK_BURGERS1D) {
     if (pr->ny != 1 || pr->nx < 3) return no("burgers1d needs nx >= 3 and ny == 1");
   } else if (pr->nx < 3 || pr->ny < 3) {
@@ -20,23 +20,39 @@ bool make_probdev(const jfnk_problem* pr, ProbDev* P, std::string* why) {
   }
   if ((long long)pr->nx * pr->ny > (1LL << 30)) return no("grid too large");
   const bool bvp = (pde == JFNK_MAXWELL_TE2D);
-  if (!bvp && !(pr->dt > 0.0 && pr->theta >= 0.0 && pr->theta <= 1.0 && std::isfinite(pr->dt)))
-    return no("time step needs dt > 0 and 0 <= theta <= 1");
+  const bool cfl = (pde == JFNK_BURGERS2D && pr->p[2] > 0.0);
+  if (!bvp && !(pr->theta >= 0.0 && pr->theta <= 1.0)) return no("time step needs 0 <= theta <= 1");
+  if (!bvp && !cfl && !(pr->dt > 0.0 && std::isfinite(pr->dt))) return no("time step needs dt > 0");
+  if (pde == JFNK_BURGERS2D) {
+    if (!(pr->p[0] >= 0.0 && std::isfinite(pr->p[0]))) return no("burgers2d needs nu >= 0");
+    if (!(pr->p[1] >= 0.0 && std::isfinite(pr->p[1]))) return no("burgers2d needs L >= 0 (0: 2 pi)");
+    if (!(pr->p[2] >= 0.0 && std::isfinite(pr->p[2]))) return no("burgers2d needs a Courant number C >= 0");
+  }
   if (pde == JFNK_SU_OLSON2D && !(pr->p[0] > 0.0 && pr->p[1] > 0.0)) return no("su_olson needs sigma > 0 and a > 0");
   if (pde == JFNK_MAXWELL_TE2D && !(pr->p[0] > 0.0)) return no("maxwell needs k > 0");
   std::memset(P, 0, sizeof(*P));
   P->pde = pde;
   P->nx = pr->nx;
   P->ny = pr->ny;
-  P->nf = (pde == JFNK_SU_OLSON2D || pde == JFNK_MAXWELL_TE2D) ? 2 : 1;
+  P->nf = pde_nfields(pde);
   P->ncell = (long long)pr->nx * pr->ny;
   P->bvp = bvp ? 1 : 0;
-  P->thdt = bvp ? 1.0 : pr->theta * pr->dt;
-  P->c_old = bvp ? 0.0 : (1.0 - pr->theta) * pr->dt;
-  P->invhx = (double)pr->nx;
-  P->invhy = (double)pr->ny;
-  P->invhx2 = (double)pr->nx * (double)pr->nx;
-  P->invhy2 = (double)pr->ny * (double)pr->ny;
+  P->theta = bvp ? 0.0 : pr->theta;
+  P->cfl = cfl ? pr->p[2] : 0.0;
+  if (bvp) {
+    P->thdt = 1.0;
+    P->c_old = 0.0;
+  } else {
+    set_dt(P, cfl ? 0.0 : pr->dt);   // an adaptive step is installed before each implicit step
+  }
+  double side = 1.0;
+  if (pde == JFNK_BURGERS2D) side = pr->p[1] > 0.0 ? pr->p[1] : 6.283185307179586;
+  P->hx = side / pr->nx;
+  P->hy = side / pr->ny;
+  P->invhx = pr->nx / side;
+  P->invhy = pr->ny / side;
+  P->invhx2 = P->invhx * P->invhx;
+  P->invhy2 = P->invhy * P->invhy;
   P->p0 = pr->p[0]; P->p1 = pr->p[1]; P->p2 = pr->p[2]; P->p3 = pr->p[3];
   if (pde == JFNK_SU_OLSON2D) {
     P->flag = pr->p[4] != 0.0;

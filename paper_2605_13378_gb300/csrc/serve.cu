@@ -36,7 +36,7 @@ Server::~Server() {
 jfnk_status Server::submit(const jfnk_problem* prob, const jfnk_opts* opts, const double* x0, double* x_out,
                            int steps, unsigned long long* ticket) {
   const long long cells = (long long)prob->nx * prob->ny *
-                          ((prob->pde == JFNK_SU_OLSON2D || prob->pde == JFNK_MAXWELL_TE2D) ? 2 : 1);
+                          pde_nfields(prob->pde);
   const bool batched = cells <= batch_max_cells_ && BatchEngine::supports(prob, opts, nullptr) &&
                        (prob->pde == JFNK_MAXWELL_TE2D || steps >= 1);
   const size_t need = batched ? BatchEngine::workspace_bytes(prob, opts) : workspace_estimate(prob, opts);

@@ -610,5 +610,7 @@ cudaError_t stencil_su_olson(int mode, const ProbDev& P, int t, int tv, const St
                              cudaStream_t st);
 cudaError_t stencil_maxwell(int mode, const ProbDev& P, int t, int tv, const StencilArgs& a, RedWs red,
                             cudaStream_t st);
+cudaError_t stencil_burgers2d(int mode, const ProbDev& P, int t, int tv, const StencilArgs& a, RedWs red,
+                              cudaStream_t st);
 
 }  // namespace jfnk

@@ -25,7 +25,7 @@ JFNK_OK, JFNK_E_INVALID, JFNK_E_OOM, JFNK_E_CUDA, JFNK_E_NOT_CONVERGED = 0, 1, 2
 JFNK_E_BREAKDOWN, JFNK_E_NONFINITE, JFNK_E_LINESEARCH, JFNK_E_TIMEOUT, JFNK_E_BUSY = 5, 6, 7, 8, 9
 JFNK_AD, JFNK_FD = 0, 1
 JFNK_GMRES, JFNK_BICGSTAB, JFNK_CG = 0, 1, 2
-JFNK_BURGERS1D, JFNK_ALLEN_CAHN2D, JFNK_SU_OLSON2D, JFNK_MAXWELL_TE2D = 0, 1, 2, 3
+JFNK_BURGERS1D, JFNK_ALLEN_CAHN2D, JFNK_SU_OLSON2D, JFNK_MAXWELL_TE2D, JFNK_BURGERS2D = 0, 1, 2, 3, 4
 JFNK_FP64, JFNK_FP32, JFNK_MIXED_FP32, JFNK_MIXED_BF16 = 0, 1, 2, 3
 JFNK_EPS_SCALED, JFNK_EPS_PAPER = 0, 1
 JFNK_CGS2, JFNK_DCGS2 = 0, 1
@@ -53,7 +53,7 @@ class jfnk_report(C.Structure):
     _fields_ = [("status", C.c_int), ("steps_done", C.c_int), ("steps_failed", C.c_int), ("newton_its", C.c_int),
                 ("krylov_its", C.c_int), ("jvp_calls", C.c_int), ("ls_backtracks", C.c_int),
                 ("ls_failures", C.c_int), ("krylov_failures", C.c_int), ("res0", C.c_double),
-                ("res_final", C.c_double), ("ms", C.c_double)]
+                ("res_final", C.c_double), ("ms", C.c_double), ("dt_last", C.c_double)]
 
     def as_dict(self) -> dict:
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -221,7 +221,7 @@ def jfnk_batch_stats(ctx: int, pde: int = 0, prec: int = 0, nx: int = 0, ny: int
 # --- small conveniences over the same calls ------------------------------------------------------
 
 PDE_IDS = {"burgers1d": JFNK_BURGERS1D, "allen_cahn": JFNK_ALLEN_CAHN2D, "su_olson": JFNK_SU_OLSON2D,
-           "maxwell": JFNK_MAXWELL_TE2D}
+           "maxwell": JFNK_MAXWELL_TE2D, "burgers2d": JFNK_BURGERS2D}
 
 
 def make_problem(pde: str, nx: int, ny: int = 1, dt: float = 0.0, theta: float = 1.0, params=(),

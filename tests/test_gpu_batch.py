@@ -3,7 +3,7 @@
 jfnk_solve_batch advances many independent Newton-GMRES solves together, one
 phase of each per kernel launch, with every solve's control state on the
 device. Its parity bar is the single-solve one: each problem of a mixed batch
-(four PDEs, FP64 / FP32 / mixed FP32, AD and FD) is compared with the oracle
+(five PDEs, FP64 / FP32 / mixed FP32, AD and FD, fixed and adaptive CFL steps) is compared with the oracle
 on the same seeded input (solution to 1e-10 in FP64, 1e-5 in reduced
 precision; Newton counts equal in FP64; Krylov counts within 2 per Newton
 step, or inside the oracle's own perturbation band for the radiation problem).
@@ -87,6 +87,19 @@ def _cases(J):
     c.append(("maxwell_born", J.make_problem("maxwell", nm, nm, 0.0, 1.0, (k, chi), eps_r=eps, source=f),
               _opts(J, J.JFNK_FP64, "ad", 60, 1e-8, 1e-8, 50, 30), np.zeros(2 * nm * nm), 1, mx_oracle, 1e-8,
               True, "no_krylov"))
+    # 2D Burgers: fixed step (TGV), adaptive CFL step (DSL, FD), adaptive mixed precision (4VC)
+    nb = 40
+    t0, d0, v0 = (si.burgers2d_ic(nb, nb, k) for k in ("tgv", "dsl", "4vc"))
+    b2 = lambda C, dt=0.05: opdes.Burgers2D(nx=nb, ny=nb, nu=0.05, dt=dt, theta=0.5, courant=C)
+    c.append(("burgers2d_tgv", J.make_problem("burgers2d", nb, nb, 0.05, 0.5, (0.05, 0.0, 0.0)),
+              _opts(J, J.JFNK_FP64, "ad"), t0, 3,
+              lambda: onw.time_steps(b2(0.0), t0, 3, _oopts("ad")), 1e-10, True, None))
+    c.append(("burgers2d_dsl_cfl_fd", J.make_problem("burgers2d", nb, nb, 0.0, 0.5, (0.05, 0.0, 1.0)),
+              _opts(J, J.JFNK_FP64, "fd"), d0, 3,
+              lambda: onw.time_steps(b2(1.0), d0, 3, _oopts("fd")), 1e-10, True, None))
+    c.append(("burgers2d_4vc_cfl_mixed", J.make_problem("burgers2d", nb, nb, 0.0, 0.5, (0.05, 0.0, 1.0)),
+              _opts(J, J.JFNK_MIXED_FP32, "ad", 30, 1e-9, 1e-5, max_newton=30), v0, 2,
+              lambda: onw.time_steps(b2(1.0), v0, 2, _oopts("ad", 30, 1e-12, 1e-12)), 1e-5, False, None))
     return c
 
 

@@ -66,6 +66,11 @@ def _case(name, nx, ny, seed=0):
         x = np.concatenate([rng.uniform(0.05, 1.0, nx * ny), rng.uniform(0.2, 1.0, nx * ny)])
         lp = J.make_problem("su_olson", nx, ny, 1e-2, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
         extra = None
+    elif name == "burgers2d":
+        p = opdes.Burgers2D(nx=nx, ny=ny, nu=0.02, dt=0.05, theta=0.5)
+        x = rng.uniform(-1.0, 1.0, 2 * nx * ny)
+        lp = J.make_problem("burgers2d", nx, ny, 0.05, 0.5, (0.02, 0.0, 0.0))
+        extra = None
     else:
         eps = si.maxwell_medium(nx, ny, seed)
         f = si.maxwell_point_source(nx, ny)
@@ -82,7 +87,7 @@ def _case(name, nx, ny, seed=0):
 # odd row lengths take the gather launch form, multiples of 4 the march form (16-byte row vectors)
 CASES = [("burgers", 1000, 1), ("allen_cahn", 70, 45), ("su_olson", 67, 41), ("maxwell", 66, 37),
          ("burgers", 996, 1), ("allen_cahn", 68, 44), ("su_olson", 72, 40), ("maxwell", 64, 37),
-         ("su_olson", 40, 40), ("maxwell", 96, 9)]
+         ("su_olson", 40, 40), ("maxwell", 96, 9), ("burgers2d", 70, 45), ("burgers2d", 64, 37)]
 
 
 def _dev(a, dtype=torch.float64):
@@ -210,3 +215,8 @@ def test_invalid_problems_are_rejected(J, ctx):
     assert J.jfnk_set_problem(ctx, J.make_problem("allen_cahn", 16, 16, -0.1, 0.5, (1e-3, 1.0))) == J.JFNK_E_INVALID
     assert "dt" in J.jfnk_last_error(ctx)
     assert J.jfnk_set_problem(ctx, J.make_problem("maxwell", 16, 16, 0.0, 1.0, (0.0, 0.1))) == J.JFNK_E_INVALID
+    assert J.jfnk_set_problem(ctx, J.make_problem("burgers2d", 16, 16, 0.1, 0.5, (-0.1, 0.0, 0.0))) == J.JFNK_E_INVALID
+    assert "nu" in J.jfnk_last_error(ctx)
+    assert J.jfnk_set_problem(ctx, J.make_problem("burgers2d", 16, 16, 0.0, 0.5, (0.1, 0.0, 0.0))) == J.JFNK_E_INVALID
+    # with a Courant number the step is adaptive and dt is not needed
+    assert J.jfnk_set_problem(ctx, J.make_problem("burgers2d", 16, 16, 0.0, 0.5, (0.1, 0.0, 1.0))) == J.JFNK_OK
