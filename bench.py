@@ -73,7 +73,7 @@ def _args():
     ap.add_argument("--suite", action="store_true",
                     help="the paper's 2D Burgers suite (TGV, DSL, 4VC x nu x grid) over eight solver variants, "
                          "with Dolan-More performance profiles, instead of the benchmark")
-    ap.add_argument("--suite-steps", type=int, default=10, help="implicit steps per suite run")
+    ap.add_argument("--suite-steps", type=int, default=100, help="implicit steps per suite run")
     ap.add_argument("--suite-grids", default="256,512", help="grid sizes of the suite")
     return ap.parse_args()
 
