@@ -660,7 +660,7 @@ def main() -> None:
         "config": {"workload": WORKLOAD, "grid": [N_GRID, N_GRID], "steps_per_run": a.steps,
                    "form": "mixed: FP32 AD JVP + FP32 GMRES(40) basis, FP64 Newton residual/update/line search/"
                            "Hessenberg", "tol_newton": TOL_NEWTON, "tol_krylov": TOL_KRYLOV["mixed"],
-                   "arnoldi": a.ortho,
+                   "arnoldi": (a.ortho + "-fused") if "arnoldi_dcgs_fused" in kern else a.ortho,
                    "l2": "inputs larger than L2 (GMRES basis 656 MB, state 32 MB per vector)",
                    "parallelism": f"replicas x{world}"},
         "p50_ms": p50, "p99_ms": p99,

@@ -23,7 +23,8 @@ SOURCES = ["stencil.cu", "stencil_burgers.cu", "stencil_allen_cahn.cu", "stencil
            "stencil_burgers2d.cu",
            "krylov.cu", "stream_f64.cu", "stream_f32.cu", "stream_bf16.cu", "jfnk.cu", "serve.cu",
            "noalloc.cu", "problem.cu", "batch.cu", "batch_burgers.cu", "batch_allen_cahn.cu", "batch_su_olson.cu",
-           "batch_maxwell.cu", "batch_burgers2d.cu"]
+           "batch_maxwell.cu", "batch_burgers2d.cu", "dcgs_fused.cu", "dcgs_fused_allen_cahn.cu",
+           "dcgs_fused_maxwell.cu", "dcgs_fused_burgers2d.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-lineinfo", "-std=c++17", "--extended-lambda", "-Xcompiler", "-fPIC,-O2",
          "-I" + INCLUDE, "-I" + CSRC]

@@ -32,12 +32,12 @@ namespace {
 
 enum KClass {
   KC_RESIDUAL, KC_RHS, KC_JVP_AD, KC_JVP_FD, KC_ARN1, KC_ARN2, KC_ARN3, KC_GINIT, KC_GFIN, KC_CAST,
-  KC_VDOTS, KC_BICG, KC_DCGS1, KC_DCGS2, KC_CFL, KC_COUNT
+  KC_VDOTS, KC_BICG, KC_DCGS1, KC_DCGS2, KC_CFL, KC_DCGSF, KC_COUNT
 };
 const char* kKClassNames[KC_COUNT] = {
     "residual", "rhs", "jvp_ad", "jvp_fd", "arnoldi_dots", "arnoldi_update_dots", "arnoldi_update_norm_givens",
     "gmres_init", "gmres_backsolve_update", "cast", "vdots", "bicgstab_vector", "arnoldi_dcgs_dots",
-    "arnoldi_dcgs_update", "cfl_dt"};
+    "arnoldi_dcgs_update", "cfl_dt", "arnoldi_dcgs_fused"};
 
 constexpr int kLookahead = 3;   // Arnoldi / BiCGSTAB steps the host may run ahead of the device
 
@@ -104,6 +104,7 @@ struct jfnk_ctx {
     void *x = nullptr, *xt = nullptr, *xn = nullptr, *F = nullptr, *Ft = nullptr, *b = nullptr, *d = nullptr;
     void *x32 = nullptr, *x32t = nullptr, *F32 = nullptr, *b32 = nullptr;
     void *rhsk = nullptr, *w = nullptr, *dj = nullptr, *V = nullptr;
+    void *u2[2] = {nullptr, nullptr}, *w2 = nullptr;   // fused delayed-CGS2 pass: candidates, second w
     void *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     void* user = nullptr;        // FP64 staging of user arrays
     std::vector<void*> all;
@@ -219,6 +220,7 @@ jfnk_status ensure_ws(jfnk_ctx* ctx, int prec, int m, int krylov) {
   AL(w.rhsk, N * sj); AL(w.w, N * sj); AL(w.dj, N * sj);
   if (krylov == JFNK_GMRES) {
     AL(w.V, (size_t)(m + 1) * N * sb);
+    if (tj == VT_F32 && tb == VT_F32) { AL(w.u2[0], N * sj); AL(w.u2[1], N * sj); AL(w.w2, N * sj); }
   } else {
     AL(w.r, N * sj); AL(w.rhat, N * sj); AL(w.p, N * sj); AL(w.v, N * sj); AL(w.s, N * sj); AL(w.t, N * sj);
   }
@@ -378,12 +380,69 @@ struct Solver {
     return JFNK_OK;
   }
 
+  // ---- the same cycle with one pass per step (dcgs_fused.cuh): JVP and dots
+  // of u_0 as above, then per step j the update of step j, the JVP of
+  // u_{j+1} and the dots of step j + 1 in one kernel; the pass of step m - 1
+  // takes the dots of u_m without a JVP and so completes the last column.
+  // Candidates alternate between two buffers, and so do the JVP outputs.
+  // Opt-in (JFNK_FUSED=1): it reads the basis once per step instead of
+  // twice, but with one column per thread per row it is bound by instruction
+  // issue and latency, and the two streaming passes are faster on GB300.
+  bool fused_on(int m) const {
+    const char* env = std::getenv("JFNK_FUSED");   // 1: the fused pass (measured slower than two passes)
+    return env && env[0] == '1' && o.lin == JFNK_AD && o.ortho == JFNK_DCGS2 && tb == VT_F32 && tj == VT_F32 && ctx->stream_ok &&
+           ctx->ws.u2[0] && dcgs_fused_supported(P, m, ctx->nsm);
+  }
+
+  jfnk_status dcgs_cycle_fused(int m, int* steps_run) {
+    jfnk_ctx::Ws& w = ctx->ws;
+    const double nv = (double)N;
+    void* U[2] = {w.u2[0], w.u2[1]};
+    void* W[2] = {w.w, w.w2};
+    {
+      JvpArgs a = jvp_base();
+      a.v = w.V;
+      a.tv = tb;
+      a.vscale = ctx->gctl->scale;
+      a.out = W[0];
+      a.active = &ctx->gctl->active;
+      jfnk_status s = jvp(a, 0);
+      if (s) return s;
+      int ev1 = tm_begin(ctx, KC_DCGS1, nv * sb() + nv * sj(), 0);
+      cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, 0, W[0], ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream);
+      tm_end(ctx, ev1);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs dots kernel");
+      CK(cudaMemcpyAsync(U[0], w.V, (size_t)N * sj(), cudaMemcpyDeviceToDevice, ctx->stream), "copy u_0");
+    }
+    const void* X = (tj == ts) ? x : x32;
+    const double aux = (P.pde == 3 && P.eps64) ? (double)P.ncell * 4.0 : 0.0;
+    int j = 0;
+    for (; j < m; ++j) {
+      if (j >= kLookahead) {
+        CK(cudaEventSynchronize(ctx->iter_ev[(j - kLookahead) % (kLookahead + 1)]), "iteration event");
+      }
+      if (*ctx->hflag == 0) break;
+      const bool has_w = j + 1 < m;
+      // reads slots 0..j-1, u_j, w_j (and x); writes q_j, u_{j+1} (and J u_{j+1})
+      const double bytes = ((double)j + 4.0 + (has_w ? 2.0 : 0.0)) * nv * sb() + (has_w ? aux : 0.0);
+      int ev = tm_begin(ctx, KC_DCGSF, bytes, j + 1);
+      cudaError_t e = launch_dcgs_fused(P, N, w.V, j, has_w, j == 0, U[j & 1], U[(j + 1) & 1], W[j & 1],
+                                        W[(j + 1) & 1], X, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream);
+      tm_end(ctx, ev);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "fused dcgs kernel");
+      CK(cudaEventRecord(ctx->iter_ev[j % (kLookahead + 1)], ctx->stream), "event record");
+    }
+    *steps_run = j;
+    return JFNK_OK;
+  }
+
   // ---- restarted GMRES(m): J d = -F ------------------------------------
   jfnk_status gmres(int* kstatus) {
     jfnk_ctx::Ws& w = ctx->ws;
     const int m = o.restart;
     const double nv = (double)N;
     const bool streamed = ctx->stream_ok && stream_supported(N);
+    const bool fused = o.ortho == JFNK_DCGS2 && fused_on(m);
     *ctx->hflag = 1;   // before any launch that may clear it
     int ev = tm_begin(ctx, KC_GINIT, nv * (ss() + sb() + sj() + ss()), -1);
     cudaError_t e = launch_gmres_init(ts, tj, tb, td, N, F, w.V, w.rhsk, w.d, ctx->gctl, sc, o.tol_krylov, m,
@@ -429,7 +488,7 @@ struct Solver {
       }
       if (o.ortho == JFNK_DCGS2) {
         int steps_run = 0;
-        jfnk_status s = dcgs_cycle(m, &steps_run);
+        jfnk_status s = fused ? dcgs_cycle_fused(m, &steps_run) : dcgs_cycle(m, &steps_run);
         if (s) return s;
         e = cudaSuccess;
         if (steps_run > 0) {
@@ -684,6 +743,7 @@ size_t workspace_estimate(const jfnk_problem* pr, const jfnk_opts* o) {
   const size_t ss = vt_size(ts), sj = vt_size(tj), sb = vt_size(tb);
   size_t b = N * (7 * ss + 8 + 3 * sj) + (tj != ts ? 4 * N * sj : 0);
   b += (o->krylov == JFNK_GMRES) ? (size_t)(o->restart + 1) * N * sb : 6 * N * sj;
+  if (o->krylov == JFNK_GMRES && tj == VT_F32 && tb == VT_F32) b += 3 * N * sj;   // fused Arnoldi buffers
   b += (size_t)2048 * kMaxK * 8 + 65536;   // reductions and control blocks
   if (pr->pde == JFNK_MAXWELL_TE2D) b += (size_t)pr->nx * pr->ny * 3 * 12;
   return b;

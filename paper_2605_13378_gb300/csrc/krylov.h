@@ -47,6 +47,18 @@ cudaError_t dcgs_f32(int pass, long long n, void* V, int j, const void* w, Gmres
                      unsigned int* err, int nsm, cudaStream_t st);
 cudaError_t dcgs_bf16(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
                       unsigned int* err, int nsm, cudaStream_t st);
+// Fused delayed-CGS2 Arnoldi pass for the AD JVP, FP32 basis and JVP, 2D
+// PDEs with face neighbours only (Allen-Cahn, Maxwell TE, 2D Burgers):
+// q_j -> basis slot j, u_{j+1} = U_out, J u_{j+1} -> W_out (when has_w), and
+// the dots of step j + 1 with its Hessenberg step on the last CTA. u_j is read
+// from U_in and w_j from W_in (times sigma_j unless wmul_one); X is the state
+// in FP32. dcgs_fused_supported says whether every step of a GMRES(m) cycle
+// fits the pass (nx % 4 == 0, ny >= 3, shared-memory plan).
+bool dcgs_fused_supported(const ProbDev& P, int m, int nsm);
+cudaError_t launch_dcgs_fused(const ProbDev& P, long long n, void* V, int j, bool has_w, bool wmul_one,
+                              const void* U_in, void* U_out, const void* W_in, void* W_out, const void* X,
+                              GmresCtl* ctl, RedWs red, unsigned int* err, int nsm, cudaStream_t st);
+
 cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, const void* w, GmresCtl* ctl,
                         RedWs red, unsigned int* err, int nsm, cudaStream_t st);
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);

@@ -12,6 +12,11 @@ reduction order differs from the oracle's), or inside the oracle's own
 perturbation band for the radiation problem. The GPU's CGS2 and delayed-CGS2
 solves of the same problem must agree to the same tolerance, and restart
 lengths 1 and 64, the benchmark grid and the size restriction are covered.
+The fused pass (update, AD JVP and dots of the next step in one kernel,
+selected by JFNK_FUSED=1 for AD with an FP32 basis) is held to the same bars
+and compared with the default two-pass form, on grids of one and several
+column strips, restart lengths 1, 30, 40 and 64, one and two fields, periodic
+and walled boundaries.
 """
 import json
 import os
@@ -195,3 +200,103 @@ def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
     assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-8 * g["res0"]
     xs = np.array([x[i] for i in g["sample_idx"]])
     assert np.abs(xs - np.array(g["x_samples"])).max() <= 1e-9 * g["x_absmax"]
+
+
+# ---------------------------------------------------------------------------
+# The fused pass (update of step j, AD JVP of u_{j+1}, dots of step j + 1 in
+# one kernel) runs, when JFNK_FUSED=1, for AD with an FP32 basis on
+# Allen-Cahn, Maxwell and 2D Burgers grids whose rows are multiples of 4.
+# Both forms are checked against the oracle and against each other.
+
+def _both_forms(J, ctx, lp, opts, x0, steps):
+    two = _run(J, ctx, lp, opts, x0, steps)
+    os.environ["JFNK_FUSED"] = "1"
+    try:
+        fused = _run(J, ctx, lp, opts, x0, steps)
+    finally:
+        del os.environ["JFNK_FUSED"]
+    return fused, two
+
+
+@pytest.mark.parametrize("prec", ["mixed", "fp32"])
+@pytest.mark.parametrize("nx,ny,m", [(72, 72, 40), (512, 64, 30), (68, 44, 64), (64, 48, 1)])
+def test_fused_pass_allen_cahn(J, ctx, prec, nx, ny, m):
+    u0 = si.allen_cahn_ic(nx, ny, 7)
+    p = opdes.AllenCahn2D(nx=nx, ny=ny, D=1e-3, dt=0.1, theta=0.5)
+    lp = J.make_problem("allen_cahn", nx, ny, 0.1, 0.5, (1e-3, 1.0))
+    code = J.JFNK_MIXED_FP32 if prec == "mixed" else J.JFNK_FP32
+    tol_n = 1e-9 if prec == "mixed" else 1e-4
+    tol_k = 1e-5 if m > 1 else 1e-4
+    o = _opts(J, code, "ad", m, tol_n, tol_k, max_newton=30, max_krylov=3000)
+    (s1, x1, r1), (s2, x2, r2) = _both_forms(J, ctx, lp, o, u0, 1)
+    assert s1 == J.JFNK_OK and s2 == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, u0, 1, _oopts("ad", max(m, 1), 1e-12, 1e-12, max_krylov=3000))
+    if prec == "fp32":
+        # an FP32 state meets ||F|| <= 1e-4 ||F0|| (the paper's FP32 Newton tolerance): bound the true residual
+        for x in (x1, x2):
+            assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 3.0 * tol_n * reps[0].res0
+        return
+    for x in (x1, x2):
+        assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5
+    assert np.abs(x1 - x2).max() <= 1e-5 * np.abs(x2).max()
+    if prec == "mixed":
+        assert np.linalg.norm(p.residual(x1, p.rhs(u0))) <= tol_n * reps[0].res0 * 1.0001
+        assert r1.newton_its == r2.newton_its
+        assert abs(r1.krylov_its - r2.krylov_its) <= 2 * r1.newton_its + 0.02 * r2.krylov_its
+
+
+@pytest.mark.parametrize("kind", ["tgv", "4vc"])
+def test_fused_pass_burgers2d(J, ctx, kind):
+    n, ny, nu = 64, 48, 0.02
+    x0 = si.burgers2d_ic(n, ny, kind)
+    p = opdes.Burgers2D(nx=n, ny=ny, nu=nu, courant=1.0)
+    lp = J.make_problem("burgers2d", n, ny, 0.0, 0.5, (nu, 0.0, 1.0))
+    o = _opts(J, J.JFNK_MIXED_FP32, "ad", 30, 1e-9, 1e-5, max_newton=30)
+    (s1, x1, r1), (s2, x2, r2) = _both_forms(J, ctx, lp, o, x0, 2)
+    assert s1 == J.JFNK_OK and s2 == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, reps = onw.time_steps(p, x0, 2, _oopts("ad", 30, 1e-12, 1e-12))
+    for x in (x1, x2):
+        assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5
+    assert r1.newton_its == r2.newton_its
+    assert r1.dt_last == pytest.approx(p.dt, rel=1e-6)
+
+
+def test_fused_pass_maxwell_born(J, ctx):
+    n, k, chi = 32, 3.0, 0.1
+    eps, f = si.maxwell_medium(n, n, 0), si.maxwell_point_source(n, n)
+    p = opdes.MaxwellTE2D(nx=n, ny=n, k=k, chi3=chi, eps_r=eps, f=f)
+    lp = J.make_problem("maxwell", n, n, 0.0, 1.0, (k, chi), eps_r=eps, source=f)
+    o = _opts(J, J.JFNK_MIXED_FP32, "ad", 60, 1e-8, 1e-6, 50, 60)
+    (s1, x1, r1), (s2, x2, r2) = _both_forms(J, ctx, lp, o, np.zeros(2 * n * n), 1)
+    assert s1 == J.JFNK_OK and s2 == J.JFNK_OK, J.jfnk_last_error(ctx)
+    x_ref, oref, _ = onw.bvp_solve(p, _oopts("ad", 60, 1e-10, 1e-10, 50, 60))
+    for x in (x1, x2):
+        assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5
+    assert r1.newton_its == r2.newton_its
+
+
+def test_fused_pass_is_the_one_that_runs(J, ctx):
+    """With JFNK_FUSED=1 the mixed AD delayed-CGS2 solve of a 2048-wide grid launches the fused kernel,
+    FD does not; without it no solve does."""
+    nx, ny = 2048, 64
+    u0 = si.allen_cahn_ic(nx, ny, 1)
+    lp = J.make_problem("allen_cahn", nx, ny, 0.1, 0.5, (1e-3, 1.0))
+    for lin, env, want in (("ad", "1", True), ("fd", "1", False), ("ad", None, False)):
+        if env:
+            os.environ["JFNK_FUSED"] = env
+        J.jfnk_reset_stats(ctx)
+        J.jfnk_set_timing(ctx, True)
+        try:
+            s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_MIXED_FP32, lin, 40, 1e-8, 1e-6), u0, 1)
+        finally:
+            os.environ.pop("JFNK_FUSED", None)
+        J.jfnk_set_timing(ctx, False)
+        assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+        st = J.jfnk_kernel_stats(ctx)
+        fused = st.get("arnoldi_dcgs_fused", {}).get("launches", 0)
+        assert (fused > 0) == want, st
+        assert st["arnoldi_dcgs_dots"]["launches"] > 0
+        if want:   # one dots pass per cycle, the update passes all fused
+            assert st.get("arnoldi_dcgs_update", {}).get("launches", 0) == 0
+        else:
+            assert st["arnoldi_dcgs_update"]["launches"] > 0
