@@ -97,6 +97,34 @@ template <class A> __device__ __forceinline__ A warp_sum(A v) {
   return v;
 }
 
+// Float-float numbers: hi + lo with |lo| <= ulp(hi) / 2, about 48 significant
+// bits carried in FP32 arithmetic. Sums use Knuth's TwoSum, so adding n FP32
+// values keeps the error near n 2^-48 of their magnitude; on GB300 FP32 adds
+// run at 64 times the FP64 rate. Rounded intrinsics keep the compiler from
+// reassociating the error terms.
+struct FF { float hi, lo; };
+__device__ __forceinline__ FF ff_add(FF a, FF b) {
+  const float s = __fadd_rn(a.hi, b.hi);
+  const float bb = __fsub_rn(s, a.hi);
+  float e = __fadd_rn(__fsub_rn(a.hi, __fsub_rn(s, bb)), __fsub_rn(b.hi, bb));
+  e = __fadd_rn(e, __fadd_rn(a.lo, b.lo));
+  const float hi = __fadd_rn(s, e);
+  return FF{hi, __fsub_rn(e, __fsub_rn(hi, s))};
+}
+// Butterfly over the warp; lane 0's result is the one used (the addition is
+// not bitwise symmetric in its operands).
+__device__ __forceinline__ FF warp_sum_ff(FF v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    const FF w{__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o)};
+    v = ff_add(v, w);
+  }
+  return v;
+}
+// A float-float value stored in (and read from) an 8-byte double slot.
+__device__ __forceinline__ void ff_store(double* p, FF v) { *reinterpret_cast<float2*>(p) = make_float2(v.hi, v.lo); }
+__device__ __forceinline__ FF ff_load(const double* p) { const float2 f = *reinterpret_cast<const float2*>(p); return FF{f.x, f.y}; }
+
 // sum over b = lane, lane + 32, ... < n of p[b * stride], added in that
 // order; the loads are issued eight at a time (partials written by other
 // blocks, read through L2) so the sum costs about one L2 round trip per 256

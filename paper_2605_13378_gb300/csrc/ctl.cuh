@@ -204,7 +204,20 @@ __device__ __forceinline__ void dcgs_stage(GmresCtl* c, int j, double* sh, doubl
     col[i] = c->hprev[i];
     if (i < cj) { sh[3 * LD + i] = c->cs[i]; sh[4 * LD + i] = c->sn[i]; }
   }
-  for (int e = threadIdx.x; e < (j > 0 ? cj : 0) * LD; e += blockDim.x) hs[e] = __ldcg(&c->Hraw[e]);
+  const int ne = (j > 0 ? cj : 0) * LD;
+  for (int e0 = threadIdx.x; e0 < ne; e0 += 8 * blockDim.x) {   // eight loads in flight per thread
+    double v[8];
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      v[q] = e < ne ? __ldcg(&c->Hraw[e]) : 0.0;
+    }
+#pragma unroll
+    for (int q = 0; q < 8; ++q) {
+      const int e = e0 + q * (int)blockDim.x;
+      if (e < ne) hs[e] = v[q];
+    }
+  }
 }
 
 __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
@@ -241,7 +254,8 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
   // every thread: rho, and the completed (unrotated) column j-1 into hs
   const double alpha = sigma * sigma * S[2 * j];
   const double rho2 = alpha - s_s2;
-  const double rho = rho2 > 0.0 ? sqrt(rho2) : 0.0;
+  const double irs = rho2 > 0.0 ? rsqrt(rho2) : 0.0;   // 1 / rho: one rsqrt for rho and its reciprocal
+  const double rho = rho2 * irs;
   const bool bad = !finite_d(rho2) || !finite_d(sigma);
   const double hn = rho * isig;
   if (j > 0 && !bad) {
@@ -266,6 +280,7 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
         c->g[0] = g_prev * rho;      // r = beta rho q_0
       } else {
         double a = col[0];           // one dependent FMA per rotation on the carried entry
+#pragma unroll 4
         for (int i = 0; i < cj; ++i) {
           const double b = col[i + 1];
           const double cb = s_cs[i] * b, sb = s_sn[i] * b;
@@ -273,9 +288,9 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
           a = fma(-s_sn[i], a, cb);
         }
         const double f = a, gg = col[cj + 1];
-        const double r = sqrt(f * f + gg * gg);   // Hessenberg entries: no overflow in the squares
+        const double r2 = fma(f, f, gg * gg);     // Hessenberg entries: no overflow in the squares
         double cs = 1.0, sn = 0.0;
-        if (r != 0.0) { const double ir = 1.0 / r; cs = f * ir; sn = gg * ir; }
+        if (r2 != 0.0) { const double ir = rsqrt(r2); cs = f * ir; sn = gg * ir; }
         c->cs[cj] = cs;
         c->sn[cj] = sn;
         col[cj] = cs * f + sn * gg;
@@ -310,12 +325,14 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
       s_go = go;
     }
   } else if (!bad && has_w && rho != 0.0) {
-    // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg: warp per row
-    for (int i = warp - 1; i <= j; i += nw - 1) {
+    // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg:
+    // one thread per row, a sequential FMA chain (few FP64 operations, so the
+    // rotation that warp 0 runs meanwhile keeps the FP64 pipe)
+    const int i = (int)threadIdx.x - 32;
+    if (i <= j) {
       double z = 0.0;
-      for (int l = (i > 0 ? i - 1 : 0) + lane; l < j; l += 32) z += hs[(size_t)l * LD + i] * ss[l];
-      z = warp_sum(z);
-      if (lane == 0) zz[i] = z;
+      for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) z = fma(hs[(size_t)l * LD + i], ss[l], z);
+      zz[i] = z;
     }
   }
   __syncthreads();
@@ -326,7 +343,7 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
       c->H[(size_t)cj * LD + i] = col[i];
     }
   if (!s_go) return;
-  const double irho = 1.0 / rho;
+  const double irho = irs;
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
     const double h = (S[2 * i + 1] - zz[i]) * irho;
     c->hprev[i] = h;

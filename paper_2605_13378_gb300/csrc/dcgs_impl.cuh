@@ -12,6 +12,8 @@
 // consumer warps). Requires n % 8 == 0, like the other streaming passes.
 #pragma once
 
+#include <type_traits>
+
 #include "stream_impl.cuh"
 
 namespace jfnk {
@@ -155,12 +157,22 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     }
   }
   __syncthreads();
+  // FP32 accumulators: the block partial as a float-float pair (the cross-block
+  // sums then stay in FP32 arithmetic); FP64 accumulators: a double
+  constexpr bool kFF = std::is_same<A, float>::value;
   for (int v = tid; v < 2 * nv; v += blockDim.x) {
     const int r = v & 1, t = v >> 1;
-    double sum = 0.0;
+    if constexpr (kFF) {
+      FF sum{(float)red[4 * r][t], 0.0f};
 #pragma unroll
-    for (int q = 0; q < 4; ++q) sum += red[4 * r + q][t];
-    partials[(size_t)blockIdx.x * kMaxK + v] = sum;
+      for (int q = 1; q < 4; ++q) sum = ff_add(sum, FF{(float)red[4 * r + q][t], 0.0f});
+      ff_store(&partials[(size_t)blockIdx.x * kMaxK + v], sum);
+    } else {
+      double sum = 0.0;
+#pragma unroll
+      for (int q = 0; q < 4; ++q) sum += red[4 * r + q][t];
+      partials[(size_t)blockIdx.x * kMaxK + v] = sum;
+    }
   }
   __threadfence();
   __syncthreads();
@@ -177,42 +189,144 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   // shared memory
   const int G = (int)gridDim.x, nval = 2 * nv;
   const size_t ring = (size_t)kDcgsStages * stage_bytes;
-  const bool staged = ((size_t)G * nval + (size_t)j * (kMaxM + 1)) * sizeof(double) <= ring;
+  // partials staged value-major with a padded row, [nval][G + 1], so that the
+  // lanes of a warp summing one value read consecutive banks
+  const bool staged = ((size_t)(G + 1) * nval + (size_t)j * (kMaxM + 1)) * sizeof(double) <= ring;
   double* hs = (double*)sring;                       // completed Hessenberg columns
-  double* pr = hs + (size_t)j * (kMaxM + 1);         // [G][nval]
-  for (int e0 = tid; staged && e0 < G * nval; e0 += 8 * (int)blockDim.x) {
-    double v[8];
+  double* pr = hs + (size_t)j * (kMaxM + 1);         // [nval][G + 1]
+  // every load of the tail is issued before any store: the completed
+  // Hessenberg columns and the control state (what dcgs_stage stages), then
+  // the partials, 24 per thread (e = b nval + v advanced without divisions)
+  constexpr int LD = kMaxM + 1;
+  const int T = (int)blockDim.x, cj = j - 1, ne = (j > 0 ? cj : 0) * LD;
+  double hv[16];
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * (int)blockDim.x;
-      v[q] = e < G * nval ? __ldcg(&partials[(size_t)(e / nval) * kMaxK + (e % nval)]) : 0.0;
-    }
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + q * T;
+    hv[q] = e < ne ? __ldcg(&ctl->Hraw[e]) : 0.0;
+  }
+  double hp = 0.0, hc = 0.0, hn = 0.0;
+  if (tid < j) {
+    hp = __ldcg(&ctl->hprev[tid]);
+    if (tid < cj) { hc = __ldcg(&ctl->cs[tid]); hn = __ldcg(&ctl->sn[tid]); }
+  }
+  double c0 = 0.0, c1 = 0.0, c2 = 0.0;
+  int cm = 0, cact = 0;
+  if (tid == 0) {
+    c0 = ctl->scale[j];
+    c1 = j > 0 ? ctl->g[j - 1] : ctl->g[0];
+    c2 = ctl->target;
+    cm = ctl->m;
+    cact = ctl->active;
+  }
+  if (staged) {
+    const int total = G * nval, db = T / nval, dvv = T - db * nval;
+    int b = tid / nval, v = tid - (tid / nval) * nval;
+    for (int e0 = tid; e0 < total; e0 += 24 * T) {
+      double val[24];
+      int bq = b, vq = v;
 #pragma unroll
-    for (int q = 0; q < 8; ++q) {
-      const int e = e0 + q * (int)blockDim.x;
-      if (e < G * nval) pr[e] = v[q];
+      for (int q = 0; q < 24; ++q) {
+        const int e = e0 + q * T;
+        val[q] = e < total ? __ldcg(&partials[(size_t)bq * kMaxK + vq]) : 0.0;
+        vq += dvv;
+        bq += db;
+        if (vq >= nval) { vq -= nval; ++bq; }
+      }
+      bq = b;
+      vq = v;
+#pragma unroll
+      for (int q = 0; q < 24; ++q) {
+        const int e = e0 + q * T;
+        if (e < total) pr[(size_t)vq * (G + 1) + bq] = val[q];
+        vq += dvv;
+        bq += db;
+        if (vq >= nval) { vq -= nval; ++bq; }
+      }
+      b = bq;
+      v = vq;
     }
+  }
+#pragma unroll
+  for (int q = 0; q < 16; ++q) {
+    const int e = tid + q * T;
+    if (e < ne) hs[e] = hv[q];
+  }
+  if (tid < j) {
+    sh[2 * LD + tid] = hp;
+    if (tid < cj) { sh[3 * LD + tid] = hc; sh[4 * LD + tid] = hn; }
   }
   if (tid == 0) {
-    s_ctl[0] = ctl->scale[j];
-    s_ctl[1] = j > 0 ? ctl->g[j - 1] : ctl->g[0];
-    s_ctl[2] = ctl->target;
-    s_m = ctl->m;
-    s_active = ctl->active;
+    s_ctl[0] = c0;
+    s_ctl[1] = c1;
+    s_ctl[2] = c2;
+    s_m = cm;
+    s_active = cact;
   }
-  dcgs_stage(ctl, j, sh, hs);
   __syncthreads();
-  // warp per value, lanes over blocks in a fixed order, then the butterfly
-  for (int v = warp; v < nval; v += (int)(blockDim.x >> 5)) {
-    double sum;
-    if (staged) {
-      sum = 0.0;
-      for (int b = lane; b < G; b += 32) sum += pr[(size_t)b * nval + v];
+  // warp per value, lanes over blocks in a fixed order, then the butterfly;
+  // four values of a warp at once so that their dependent adds interleave
+  const int nw = (int)(blockDim.x >> 5);
+  for (int v0 = warp; v0 < nval; v0 += 4 * nw) {
+    if constexpr (kFF) {
+      FF sum[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+      // five blocks per lane and value loaded ahead of the dependent adds
+      for (int b0 = lane; b0 < G; b0 += 5 * 32) {
+        FF x[4][5];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const int b = b0 + 32 * k;
+            x[u][k] = FF{0.0f, 0.0f};
+            if (v < nval && b < G) x[u][k] = staged ? ff_load(&pr[(size_t)v * (G + 1) + b])
+                                                    : ff_load(&partials[(size_t)b * kMaxK + v]);
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (b0 + 32 * k < G) sum[u] = ff_add(sum[u], x[u][k]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum[u] = warp_sum_ff(sum[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+          if (v < nval) S[v] = (double)sum[u].hi + (double)sum[u].lo;
+        }
+      }
     } else {
-      sum = lane_strided_sum(partials + v, kMaxK, G, lane);
+      double sum[4] = {0.0, 0.0, 0.0, 0.0};
+      if (staged) {
+        for (int b = lane; b < G; b += 32) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const int v = v0 + u * nw;
+            if (v < nval) sum[u] += pr[(size_t)v * (G + 1) + b];
+          }
+        }
+      } else {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+          if (v < nval) sum[u] = lane_strided_sum(partials + v, kMaxK, G, lane);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum[u] = warp_sum(sum[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+          if (v < nval) S[v] = sum[u];
+        }
+      }
     }
-    sum = warp_sum(sum);
-    if (lane == 0) S[v] = sum;
   }
   __syncthreads();
   dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[1], s_ctl[2], s_m, s_active);
