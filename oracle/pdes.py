@@ -147,14 +147,27 @@ class Burgers2D(_ThetaProblem):
         return super().rhs(xn)
 
 
+def _lap5_dirichlet(u: np.ndarray, hx: float, hy: float) -> np.ndarray:
+    """5-point Laplacian on interior nodes with u = 0 on the boundary nodes; u has shape (ny, nx)."""
+    p = np.zeros((u.shape[0] + 2, u.shape[1] + 2), dtype=u.dtype)
+    p[1:-1, 1:-1] = u
+    return ((p[1:-1, 2:] - 2.0 * u + p[1:-1, :-2]) / (hx * hx)
+            + (p[2:, 1:-1] - 2.0 * u + p[:-2, 1:-1]) / (hy * hy))
+
+
 @dataclass
 class AllenCahn2D(_ThetaProblem):
-    """Allen-Cahn u_t = D lap u + u - u^3, periodic unit square, 5-point Laplacian.
+    """Allen-Cahn u_t = D lap u + u - u^3 with a 5-point Laplacian.
 
     The benchmark variant of the paper's reaction-diffusion problem
     (Sec. 3.2; App. A, Nonlinear Reaction-Diffusion), which has the sink
     -u^3 only; ``linear_coef`` = 1 adds the Allen-Cahn +u term and 0 recovers
     the paper's form D lap u - u^3.
+
+    ``dirichlet`` = False: the periodic unit square, cells of width 1/nx.
+    ``dirichlet`` = True: the paper's walls, u = 0 on the boundary of the
+    square [-1/2, 1/2]^2; the unknowns are the interior nodes
+    x_i = -1/2 + (i + 1) h, h = 1/(nx + 1) (and likewise in y).
     """
 
     nx: int = 64
@@ -163,15 +176,23 @@ class AllenCahn2D(_ThetaProblem):
     dt: float = 0.1
     theta: float = 0.5
     linear_coef: float = 1.0
+    dirichlet: bool = False
 
     @property
     def n_unknowns(self) -> int:
         return self.nx * self.ny
 
+    @property
+    def spacing(self):
+        if self.dirichlet:
+            return 1.0 / (self.nx + 1), 1.0 / (self.ny + 1)
+        return 1.0 / self.nx, 1.0 / self.ny
+
     def G(self, x):
         u = x.reshape(self.ny, self.nx)
-        hx, hy = 1.0 / self.nx, 1.0 / self.ny
-        g = self.D * _lap5_periodic(u, hx, hy) + self.linear_coef * u - u * u * u
+        hx, hy = self.spacing
+        lap = _lap5_dirichlet(u, hx, hy) if self.dirichlet else _lap5_periodic(u, hx, hy)
+        g = self.D * lap + self.linear_coef * u - u * u * u
         return g.reshape(-1)
 
 

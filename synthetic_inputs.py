@@ -83,6 +83,37 @@ def burgers2d_ic(nx: int, ny: int | None = None, kind: str = "tgv", L: float = 2
     return np.concatenate([u.reshape(-1), v.reshape(-1)])
 
 
+RD_KINDS = ("gaussian", "multigauss", "sinusoidal")
+
+
+def rd_ic(nx: int, ny: int | None = None, kind: str = "gaussian") -> np.ndarray:
+    """Initial concentration of the paper's reaction-diffusion benchmark (App. A), flat, on the
+    interior nodes x_i = -1/2 + (i + 1) / (nx + 1) of the square [-1/2, 1/2]^2 (u = 0 on its boundary).
+
+    * ``gaussian``: exp(-r^2 / s^2), s = 0.1, centred at the origin.
+    * ``multigauss``: four such peaks (s = 0.08) centred at (+-0.2, +-0.2).
+    * ``sinusoidal``: |sin(kx pi x) sin(ky pi y)| with kx = ky = 4 (even, so zero on the walls).
+    The paper names the three profiles and the sinusoidal formula; widths, centres and wave
+    numbers are this module's choice.
+    """
+    ny = nx if ny is None else ny
+    x = -0.5 + np.arange(1, nx + 1, dtype=np.float64) / (nx + 1)
+    y = -0.5 + np.arange(1, ny + 1, dtype=np.float64) / (ny + 1)
+    X, Y = np.meshgrid(x, y)
+    if kind == "gaussian":
+        u = np.exp(-(X * X + Y * Y) / 0.1 ** 2)
+    elif kind == "multigauss":
+        u = np.zeros_like(X)
+        for cx in (-0.2, 0.2):
+            for cy in (-0.2, 0.2):
+                u += np.exp(-((X - cx) ** 2 + (Y - cy) ** 2) / 0.08 ** 2)
+    elif kind == "sinusoidal":
+        u = np.abs(np.sin(4 * math.pi * X) * np.sin(4 * math.pi * Y))
+    else:
+        raise ValueError(f"unknown reaction-diffusion initial condition {kind!r}")
+    return u.reshape(-1)
+
+
 def allen_cahn_ic(nx: int, ny: int | None = None, seed: int = 0) -> np.ndarray:
     """Uniform noise in [-0.1, 0.1] on an nx x ny periodic grid (flat, row-major)."""
     ny = nx if ny is None else ny
