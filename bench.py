@@ -70,9 +70,10 @@ def _args():
                     help="instead of the timed benchmark: Newton/Krylov counts and completion per configuration, "
                          "AD vs FD, one JSON line")
     ap.add_argument("--config-seeds", type=int, default=32, help="Allen-Cahn seeds for the completion rate")
-    ap.add_argument("--suite", action="store_true",
-                    help="the paper's 2D Burgers suite (TGV, DSL, 4VC x nu x grid) over eight solver variants, "
-                         "with Dolan-More performance profiles, instead of the benchmark")
+    ap.add_argument("--suite", choices=["burgers2d", "rd"], default=None,
+                    help="one of the paper's benchmark suites instead of the benchmark: 2D Burgers (TGV, DSL, "
+                         "4VC x nu x grid) or reaction-diffusion with Dirichlet walls (Gaussian, multi-Gaussian, "
+                         "sinusoidal x D x grid), over the solver variants, with Dolan-More performance profiles")
     ap.add_argument("--suite-steps", type=int, default=100, help="implicit steps per suite run")
     ap.add_argument("--suite-grids", default="256,512", help="grid sizes of the suite")
     return ap.parse_args()
@@ -379,6 +380,9 @@ def config_sweep(a) -> None:
 
 
 SUITE_VARIANTS = [(prec, lin, kr) for prec in ("fp64", "fp32") for lin in ("ad", "fd") for kr in ("gmres", "bicgstab")]
+# the reaction-diffusion Jacobian is SPD, so CG joins the comparison
+SUITE_VARIANTS_SPD = [(prec, lin, kr) for prec in ("fp64", "fp32") for lin in ("ad", "fd")
+                      for kr in ("gmres", "bicgstab", "cg")]
 PROFILE_TAUS = (1.0, 1.5, 2.0, 4.0, 8.0, 16.0, 32.0, 64.0, 128.0, 1024.0)
 
 
@@ -413,10 +417,15 @@ def performance_profile(times: dict, taus=PROFILE_TAUS) -> dict:
     return {"taus": list(taus), "problems": len(problems), "profiles": out}
 
 
-def burgers2d_suite(a) -> None:
-    """The paper's 2D Burgers benchmark (App. A): TGV, DSL and 4VC at nu in {0.1, 0.05, 0.01} on the GPU grids,
-    Courant number 1, Crank-Nicolson, solved by each of {FP64, FP32} x {AD, FD} x {GMRES(30), BiCGSTAB} with the
-    paper's tolerances and caps; Dolan-More profiles by wall time and by Krylov iterations."""
+def paper_suite(a) -> None:
+    """One of the paper's benchmark suites (App. A; Sec. 4 setup) at Courant number 1, Crank-Nicolson, each
+    run one jfnk_solve of --suite-steps implicit steps with the paper's tolerances and caps (FP64 1e-6 / 1e-8,
+    FP32 1e-4 / 1e-6, 15 Newton iterations, 100 Krylov cycles or iterations, GMRES(30)); Dolan-More profiles
+    by wall time and by Krylov iterations.
+
+    burgers2d: TGV, DSL and 4VC at nu in {0.1, 0.05, 0.01}, adaptive CFL step, {FP64, FP32} x {AD, FD} x
+    {GMRES, BiCGSTAB}. rd: u_t = D lap u - u^3 with Dirichlet walls, Gaussian, multi-Gaussian and sinusoidal
+    data at D in {0.1, 0.01, 0.001}, dt = dx^2 / D, the same variants and CG."""
     import torch
     import synthetic_inputs as si
     from paper_2605_13378_gb300 import jfnk as J
@@ -426,18 +435,31 @@ def burgers2d_suite(a) -> None:
     steps = a.suite_steps
     fatal_codes = {J.JFNK_E_NONFINITE, J.JFNK_E_BREAKDOWN, J.JFNK_E_CUDA, J.JFNK_E_TIMEOUT, J.JFNK_E_OOM,
                    J.JFNK_E_INVALID}
+    kr_code = {"gmres": J.JFNK_GMRES, "bicgstab": J.JFNK_BICGSTAB, "cg": J.JFNK_CG}
+    kr_name = {"gmres": "GMRES", "bicgstab": "BiCGSTAB", "cg": "CG"}
+    if a.suite == "burgers2d":
+        kinds, params, variants = si.BURGERS2D_KINDS, (0.1, 0.05, 0.01), SUITE_VARIANTS
+
+        def problem(n, kind, nu):
+            return (f"{kind} nu={nu:g} {n}^2", J.make_problem("burgers2d", n, n, 0.0, 0.5, (nu, 0.0, 1.0)),
+                    si.burgers2d_ic(n, n, kind))
+    else:
+        kinds, params, variants = si.RD_KINDS, (0.1, 0.01, 0.001), SUITE_VARIANTS_SPD
+
+        def problem(n, kind, D):
+            dt = (1.0 / (n + 1)) ** 2 / D
+            return (f"{kind} D={D:g} {n}^2", J.make_problem("allen_cahn", n, n, dt, 0.5, (D, 0.0, 1.0)),
+                    si.rd_ic(n, n, kind))
     runs, t_wall, t_kry = [], {}, {}
     for n in grids:
-        for kind in si.BURGERS2D_KINDS:
-            x0 = si.burgers2d_ic(n, n, kind)
-            for nu in (0.1, 0.05, 0.01):
-                prob = f"{kind} nu={nu:g} {n}^2"
-                lp = J.make_problem("burgers2d", n, n, 0.0, 0.5, (nu, 0.0, 1.0))
+        for kind in kinds:
+            for par in params:
+                prob, lp, x0 = problem(n, kind, par)
                 J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
-                for prec, lin, kr in SUITE_VARIANTS:
+                for prec, lin, kr in variants:
                     o = J.jfnk_default_opts(J.JFNK_FP64 if prec == "fp64" else J.JFNK_FP32)
                     o.lin = J.JFNK_AD if lin == "ad" else J.JFNK_FD
-                    o.krylov = J.JFNK_GMRES if kr == "gmres" else J.JFNK_BICGSTAB
+                    o.krylov = kr_code[kr]
                     o.restart = 30
                     x = torch.tensor(x0, device="cuda")
                     rep = J.jfnk_report()
@@ -447,7 +469,7 @@ def burgers2d_suite(a) -> None:
                     torch.cuda.synchronize()
                     dt_wall = time.perf_counter() - t0
                     failed = run_failed(s == J.JFNK_OK, s in fatal_codes, steps, rep.steps_failed)
-                    var = f"{lin.upper()}-{prec.upper()}-{'GMRES' if kr == 'gmres' else 'BiCGSTAB'}"
+                    var = f"{lin.upper()}-{prec.upper()}-{kr_name[kr]}"
                     t_wall.setdefault(var, {})[prob] = None if failed else dt_wall
                     t_kry.setdefault(var, {})[prob] = None if failed else max(1, rep.krylov_its)
                     runs.append({"problem": prob, "solver": var, "status": J.jfnk_status_string(s),
@@ -455,7 +477,7 @@ def burgers2d_suite(a) -> None:
                                  "steps_failed": rep.steps_failed, "newton": rep.newton_its, "krylov": rep.krylov_its,
                                  "ls_backtracks": rep.ls_backtracks, "dt_last": rep.dt_last})
     J.jfnk_destroy(ctx)
-    out = {"mode": "suite", "pde": "burgers2d", "data": "synthetic", "steps": steps, "grids": grids,
+    out = {"mode": "suite", "pde": a.suite, "data": "synthetic", "steps": steps, "grids": grids,
            "courant": 1.0, "restart": 30, "runs": runs,
            "profile_wall_time": performance_profile(t_wall), "profile_krylov_its": performance_profile(t_kry)}
     print(json.dumps(out))
@@ -494,7 +516,7 @@ def main() -> None:
         run_reference(a)
         return
     if a.suite:
-        burgers2d_suite(a)
+        paper_suite(a)
         return
     if a.configs:
         config_sweep(a)

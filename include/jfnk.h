@@ -64,7 +64,11 @@ typedef enum { JFNK_AD = 0, JFNK_FD = 1 } jfnk_linearisation;
 typedef enum { JFNK_GMRES = 0, JFNK_BICGSTAB = 1, JFNK_CG = 2 } jfnk_krylov;
 typedef enum {
   JFNK_BURGERS1D = 0,     /* p[0] = nu                                              */
-  JFNK_ALLEN_CAHN2D = 1,  /* p[0] = D, p[1] = coefficient of the +u term (1 or 0)   */
+  JFNK_ALLEN_CAHN2D = 1,  /* p[0] = D, p[1] = coefficient of the +u term (1 or 0),
+                             p[2] = 0: periodic unit square (cells of width 1/nx);
+                             1: the paper's reaction-diffusion walls, u = 0 on the
+                             boundary of [-1/2, 1/2]^2, unknowns on the interior
+                             nodes (spacing 1/(nx + 1))                           */
   JFNK_SU_OLSON2D = 2,    /* p[0] = sigma, p[1] = a, p[2] = T_b, p[3] = rho,
                              p[4] = 1 flux limiter on / 0 off                        */
   JFNK_MAXWELL_TE2D = 3,  /* p[0] = k, p[1] = chi3; aux[0] = eps_r (nx*ny),

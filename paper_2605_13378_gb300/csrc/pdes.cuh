@@ -142,7 +142,9 @@ struct Burgers2D {
 
 // ---------------------------------------------------------------------------
 // Allen-Cahn u_t = D lap u + c u - u^3 (c = 1; c = 0 is the paper's
-// reaction-diffusion sink), periodic unit square, 5-point Laplacian.
+// reaction-diffusion sink), 5-point Laplacian: periodic unit square, or
+// (P.flag) homogeneous Dirichlet walls, the unknowns being the interior
+// nodes, so that a neighbour beyond a wall is 0.
 // ---------------------------------------------------------------------------
 struct AllenCahn2D {
   static constexpr int NF = 1;
@@ -150,10 +152,17 @@ struct AllenCahn2D {
   static constexpr int POLICY = BP_WRAP;
   static constexpr bool AUX = false;
   template <class T, class V>
-  __device__ __forceinline__ static void cell(const ProbDev& P, int, int, const Nb<V, 1>& q, const CellAux<T>&,
-                                              V* M, V* G) {
+  __device__ __forceinline__ static void cell(const ProbDev& P, int i, int j, const Nb<V, 1>& q,
+                                              const CellAux<T>&, V* M, V* G) {
     const V u = q.c[0];
-    V lap = (q.e[0] - T(2) * u + q.w[0]) * T(P.invhx2) + (q.n[0] - T(2) * u + q.s[0]) * T(P.invhy2);
+    V e = q.e[0], w = q.w[0], n = q.n[0], s = q.s[0];
+    if (P.flag) {
+      if (i == 0) w = V(T(0));
+      if (i == P.nx - 1) e = V(T(0));
+      if (j == 0) s = V(T(0));
+      if (j == P.ny - 1) n = V(T(0));
+    }
+    V lap = (e - T(2) * u + w) * T(P.invhx2) + (n - T(2) * u + s) * T(P.invhy2);
     M[0] = u;
     G[0] = T(P.p0) * lap + T(P.p1) * u - u * u * u;
   }

@@ -47,10 +47,13 @@ bool make_probdev(const jfnk_problem* pr, ProbDev* P, std::string* why) {
   }
   double side = 1.0;
   if (pde == JFNK_BURGERS2D) side = pr->p[1] > 0.0 ? pr->p[1] : 6.283185307179586;
-  P->hx = side / pr->nx;
-  P->hy = side / pr->ny;
-  P->invhx = pr->nx / side;
-  P->invhy = pr->ny / side;
+  // Dirichlet walls of the reaction-diffusion form: nx interior nodes, nx + 1 intervals
+  const int wall = (pde == JFNK_ALLEN_CAHN2D && pr->p[2] != 0.0) ? 1 : 0;
+  if (wall) P->flag = 1;
+  P->hx = side / (pr->nx + wall);
+  P->hy = side / (pr->ny + wall);
+  P->invhx = (pr->nx + wall) / side;
+  P->invhy = (pr->ny + wall) / side;
   P->invhx2 = P->invhx * P->invhx;
   P->invhy2 = P->invhy * P->invhy;
   P->p0 = pr->p[0]; P->p1 = pr->p[1]; P->p2 = pr->p[2]; P->p3 = pr->p[3];

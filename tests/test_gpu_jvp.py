@@ -66,6 +66,11 @@ def _case(name, nx, ny, seed=0):
         x = np.concatenate([rng.uniform(0.05, 1.0, nx * ny), rng.uniform(0.2, 1.0, nx * ny)])
         lp = J.make_problem("su_olson", nx, ny, 1e-2, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
         extra = None
+    elif name == "rd_dirichlet":
+        p = opdes.AllenCahn2D(nx=nx, ny=ny, D=1e-2, dt=0.05, theta=0.5, linear_coef=0.0, dirichlet=True)
+        x = rng.uniform(-1.0, 1.0, nx * ny)
+        lp = J.make_problem("allen_cahn", nx, ny, 0.05, 0.5, (1e-2, 0.0, 1.0))
+        extra = None
     elif name == "burgers2d":
         p = opdes.Burgers2D(nx=nx, ny=ny, nu=0.02, dt=0.05, theta=0.5)
         x = rng.uniform(-1.0, 1.0, 2 * nx * ny)
@@ -87,7 +92,8 @@ def _case(name, nx, ny, seed=0):
 # odd row lengths take the gather launch form, multiples of 4 the march form (16-byte row vectors)
 CASES = [("burgers", 1000, 1), ("allen_cahn", 70, 45), ("su_olson", 67, 41), ("maxwell", 66, 37),
          ("burgers", 996, 1), ("allen_cahn", 68, 44), ("su_olson", 72, 40), ("maxwell", 64, 37),
-         ("su_olson", 40, 40), ("maxwell", 96, 9), ("burgers2d", 70, 45), ("burgers2d", 64, 37)]
+         ("su_olson", 40, 40), ("maxwell", 96, 9), ("burgers2d", 70, 45), ("burgers2d", 64, 37),
+         ("rd_dirichlet", 70, 45), ("rd_dirichlet", 64, 37)]
 
 
 def _dev(a, dtype=torch.float64):
