@@ -221,7 +221,7 @@ __device__ __forceinline__ void dcgs_stage(GmresCtl* c, int j, double* sh, doubl
 }
 
 __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
-                                          double sigma, double g_prev, double target, int m, int active0) {
+                                          double sigma, double g_prev, double target, int m, int active0, int its0) {
   constexpr int LD = kMaxM + 1;
   double* ss = sh;             // s
   double* zz = sh + LD;        // z
@@ -299,7 +299,7 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
         c->g[cj + 1] = g1;
         c->g[cj] = cs * g_prev;
         c->k = j;
-        c->its += 1;
+        c->its = its0 + 1;                   // its0 staged with the other scalars: no load on this path
         const double res = fabs(g1);
         c->resid = res;
         if (!finite_d(res) || !finite_d(hn)) {

@@ -398,7 +398,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
   __shared__ double Sd[2 * (kMaxM + 1)];
   __shared__ double sh[5 * (kMaxM + 1)];
   __shared__ double s_ctl[3];
-  __shared__ int s_m, s_active;
+  __shared__ int s_m, s_active, s_its;
   const int GB = (int)gridDim.x;
   const size_t ringb = (size_t)S * G.stage_bytes;
   const bool staged = ((size_t)GB * nval + (size_t)jj * (kMaxM + 1)) * sizeof(double) <= ringb;
@@ -437,6 +437,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
     s_ctl[2] = a.ctl->target;
     s_m = a.ctl->m;
     s_active = a.ctl->active;
+    s_its = a.ctl->its;
   }
   __syncthreads();
   if (!s_active) {
@@ -447,7 +448,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
   for (int i = tid; i <= jj; i += blockDim.x) Sd[2 * i + 1] *= sigma;   // dots with J (sigma u_{j+1})
   dcgs_stage(a.ctl, jj, sh, hs);
   __syncthreads();
-  dcgs_step(a.ctl, jj, Sd, has_w, sh, hs, sigma, s_ctl[1], s_ctl[2], s_m, s_active);
+  dcgs_step(a.ctl, jj, Sd, has_w, sh, hs, sigma, s_ctl[1], s_ctl[2], s_m, s_active, s_its);
   __syncthreads();
   if (tid == 0) *a.counter = 0u;
 }

@@ -183,7 +183,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   __shared__ double S[2 * (kMaxM + 1)];
   __shared__ double sh[5 * (kMaxM + 1)];
   __shared__ double s_ctl[3];
-  __shared__ int s_m, s_active;
+  __shared__ int s_m, s_active, s_its;
   // one round of loads: every block's partials into the drained ring (when
   // they fit beside the completed Hessenberg columns), the control state into
   // shared memory
@@ -211,13 +211,14 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     if (tid < cj) { hc = __ldcg(&ctl->cs[tid]); hn = __ldcg(&ctl->sn[tid]); }
   }
   double c0 = 0.0, c1 = 0.0, c2 = 0.0;
-  int cm = 0, cact = 0;
+  int cm = 0, cact = 0, cits = 0;
   if (tid == 0) {
     c0 = ctl->scale[j];
     c1 = j > 0 ? ctl->g[j - 1] : ctl->g[0];
     c2 = ctl->target;
     cm = ctl->m;
     cact = ctl->active;
+    cits = ctl->its;
   }
   if (staged) {
     const int total = G * nval, db = T / nval, dvv = T - db * nval;
@@ -262,6 +263,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     s_ctl[2] = c2;
     s_m = cm;
     s_active = cact;
+    s_its = cits;
   }
   __syncthreads();
   // warp per value, lanes over blocks in a fixed order, then the butterfly;
@@ -329,7 +331,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     }
   }
   __syncthreads();
-  dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[1], s_ctl[2], s_m, s_active);
+  dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[1], s_ctl[2], s_m, s_active, s_its);
   __syncthreads();
   if (tid == 0) *counter = 0u;
 }
