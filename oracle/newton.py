@@ -92,7 +92,8 @@ def _right_preconditioned(problem, x, A, opt: Options):
     if opt.precond != "cslp":
         raise ValueError(opt.precond)
     minv = 1.0 / problem.cslp_diag(x, opt.precond_damping)
-    P = lambda y: _pdes.apply_cell_complex(minv, y)
+    apply = getattr(problem, "apply_diag", None) or _pdes.apply_cell_complex
+    P = lambda y: apply(minv, y)
     return (lambda v: A(P(v))), P
 
 
@@ -182,8 +183,11 @@ def born_start(problem, opt: Options):
     """Initial guess for the Maxwell problem: the chi3 = 0 linear problem solved from zero.
 
     Returns (x_born, Report of that linear solve)."""
-    lin = copy.copy(problem)
-    lin.chi3 = 0.0
+    if hasattr(problem, "born"):
+        lin = problem.born()
+    else:
+        lin = copy.copy(problem)
+        lin.chi3 = 0.0
     x0 = np.zeros(problem.n_unknowns)
     F0 = lin.residual(x0, None)
     rep = Report(res0=float(np.linalg.norm(F0)))

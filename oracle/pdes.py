@@ -357,6 +357,128 @@ class MaxwellTE2D(_ThetaProblem):
         return -(2.0 / (hx * hx) + 2.0 / (hy * hy)) + self.k * self.k * eps_e * (1.0 - damping * 1j)
 
 
+@dataclass
+class MaxwellVecTE2D(_ThetaProblem):
+    """The paper's vector TE Maxwell problem in a Kerr medium (App. A, Time-Harmonic Maxwell's Equations).
+
+    curl curl E - w^2 eps(E) E = i w J, E = (Ex, Ey), mu0 = eps0 = 1,
+    eps(E) = (1 - 0.05 i)(1 + chi |E|), |E| = sqrt(|Ex|^2 + |Ey|^2), on the
+    unit square with perfectly conducting walls, as the real map on the
+    planes [Re Ex, Im Ex, Re Ey, Im Ey]:
+      F = curl curl E - w^2 eps(E) E - i w J.
+    Nodes x_i = i h, h = 1/(n - 1), the walls being nodes. Second-order
+    central differences of (curl curl E)_x = d2 Ey/dxdy - d2 Ex/dy2 and
+    (curl curl E)_y = d2 Ex/dxdy - d2 Ey/dx2 (the mixed derivative on the four
+    corner neighbours). On the walls the tangential component's row is
+    F = E_t (PEC); the normal component keeps its equation with neighbours
+    beyond the wall taken by reflection: a tangential component odd, a normal
+    component even across the wall (the image of a perfect conductor).
+    |E| enters through a branch on its squared value: 0 where the field
+    vanishes, so the derivative there is taken as 0.
+    """
+
+    nx: int = 32
+    ny: int = 32
+    omega: float = 5.0
+    chi: float = 0.05
+    J: np.ndarray | None = None      # [Re Jx, Im Jx, Re Jy, Im Jy] planes, or None (no source)
+    bvp: bool = True
+    theta: float = 0.0
+
+    @property
+    def n_unknowns(self) -> int:
+        return 4 * self.nx * self.ny
+
+    @property
+    def spacing(self):
+        return 1.0 / (self.nx - 1), 1.0 / (self.ny - 1)
+
+    @staticmethod
+    def _pad(u, sx, sy):
+        """u (ny, nx) extended by one node per side by reflection about the wall nodes:
+        factor sx across the x walls (left, right) and sy across the y walls."""
+        p = np.zeros((u.shape[0] + 2, u.shape[1] + 2), dtype=u.dtype)
+        p[1:-1, 1:-1] = u
+        p[1:-1, 0] = sx * u[:, 1]
+        p[1:-1, -1] = sx * u[:, -2]
+        p[0, :] = sy * p[2, :]
+        p[-1, :] = sy * p[-3, :]
+        return p
+
+    def curl_curl(self, ex, ey):
+        """(curl curl E)_x, (curl curl E)_y of one real or imaginary part, on all nodes."""
+        hx, hy = self.spacing
+        px = self._pad(ex, 1.0, -1.0)   # Ex: normal to the x walls (even), tangential to the y walls (odd)
+        py = self._pad(ey, -1.0, 1.0)   # Ey: tangential to the x walls (odd), normal to the y walls (even)
+        dyy_ex = (px[2:, 1:-1] - 2.0 * ex + px[:-2, 1:-1]) / (hy * hy)
+        dxx_ey = (py[1:-1, 2:] - 2.0 * ey + py[1:-1, :-2]) / (hx * hx)
+        dxy_ey = (py[2:, 2:] - py[:-2, 2:] - py[2:, :-2] + py[:-2, :-2]) / (4.0 * hx * hy)
+        dxy_ex = (px[2:, 2:] - px[:-2, 2:] - px[2:, :-2] + px[:-2, :-2]) / (4.0 * hx * hy)
+        return dxy_ey - dyy_ex, dxy_ex - dxx_ey
+
+    def _planes(self, x):
+        n = self.nx * self.ny
+        return [x[k * n:(k + 1) * n].reshape(self.ny, self.nx) for k in range(4)]
+
+    def G(self, x):
+        a, b, c, d = self._planes(x)
+        cxa, cya = self.curl_curl(a, c)          # real parts
+        cxb, cyb = self.curl_curl(b, d)          # imaginary parts
+        s2 = a * a + b * b + c * c + d * d
+        m = np.where(s2.real > 0.0, np.sqrt(np.where(s2.real > 0.0, s2, 1.0)), 0.0)
+        e = 1.0 + self.chi * m
+        w2 = self.omega * self.omega
+        J = np.zeros(4 * self.nx * self.ny) if self.J is None else self.J
+        ja, jb, jc, jd = self._planes(J)
+        # - i w J: real part + w Im J, imaginary part - w Re J
+        F = [cxa - w2 * e * (a + 0.05 * b) + self.omega * jb,
+             cxb - w2 * e * (b - 0.05 * a) - self.omega * ja,
+             cya - w2 * e * (c + 0.05 * d) + self.omega * jd,
+             cyb - w2 * e * (d - 0.05 * c) - self.omega * jc]
+        # PEC: the tangential component's rows are E_t on the walls
+        for k, comp in ((0, a), (1, b)):        # Ex is tangential to the y walls (bottom, top)
+            F[k] = F[k].copy()
+            F[k][0, :] = comp[0, :]
+            F[k][-1, :] = comp[-1, :]
+        for k, comp in ((2, c), (3, d)):        # Ey is tangential to the x walls (left, right)
+            F[k] = F[k].copy()
+            F[k][:, 0] = comp[:, 0]
+            F[k][:, -1] = comp[:, -1]
+        return np.concatenate([f.reshape(-1) for f in F])
+
+    def cslp_diag(self, x, damping: float = 0.5):
+        """Block-diagonal complex-shifted-Laplacian preconditioner (App. A, Preconditioning):
+        per node M_xx = 2/hy^2 - w^2 eps_p, M_yy = 2/hx^2 - w^2 eps_p with eps_p = eps(E)(1 - damping i);
+        1 on the PEC rows (their Jacobian rows are the identity). Returns [M_xx, M_yy] (complex, 2 n)."""
+        a, b, c, d = self._planes(x)
+        hx, hy = self.spacing
+        s2 = a * a + b * b + c * c + d * d
+        m = np.where(s2 > 0.0, np.sqrt(np.where(s2 > 0.0, s2, 1.0)), 0.0)
+        epsp = (1.0 - 0.05j) * (1.0 + self.chi * m) * (1.0 - damping * 1j)
+        w2 = self.omega * self.omega
+        mxx = (2.0 / (hy * hy) - w2 * epsp).astype(complex)
+        myy = (2.0 / (hx * hx) - w2 * epsp).astype(complex)
+        mxx[0, :] = 1.0
+        mxx[-1, :] = 1.0
+        myy[:, 0] = 1.0
+        myy[:, -1] = 1.0
+        return np.concatenate([mxx.reshape(-1), myy.reshape(-1)])
+
+    def apply_diag(self, c, v):
+        """The planes [a, b, c, d] of v with (a + ib) times c[:n] and (c + id) times c[n:], node by node."""
+        n = self.nx * self.ny
+        zx = c[:n] * (v[:n] + 1j * v[n:2 * n])
+        zy = c[n:] * (v[2 * n:3 * n] + 1j * v[3 * n:])
+        return np.concatenate([zx.real, zx.imag, zy.real, zy.imag])
+
+    def born(self):
+        """The chi = 0 problem (the Born start of App. A: the field linearised at E = 0)."""
+        import copy as _copy
+        q = _copy.copy(self)
+        q.chi = 0.0
+        return q
+
+
 def apply_cell_complex(c, v):
     """(Re, Im) planes of v multiplied cell by cell by the complex array c."""
     n = c.size
@@ -367,4 +489,4 @@ def apply_cell_complex(c, v):
 def make(pde: str, **kw):
     """Construct a problem by name: burgers1d, burgers2d, allen_cahn, su_olson, maxwell."""
     return {"burgers1d": Burgers1D, "burgers2d": Burgers2D, "allen_cahn": AllenCahn2D,
-            "su_olson": SuOlson2D, "maxwell": MaxwellTE2D}[pde](**kw)
+            "su_olson": SuOlson2D, "maxwell": MaxwellTE2D, "maxwell_vec": MaxwellVecTE2D}[pde](**kw)

@@ -38,10 +38,12 @@ def _problems(rng):
     g = pdes.Burgers2D(nx=n, ny=n + 2, nu=0.05, dt=0.05)
     x = rng.uniform(-1, 1, g.n_unknowns)
     out.append(("burgers2d", g, x, g.rhs(x * 0.9)))
+    mv = pdes.MaxwellVecTE2D(nx=n, ny=n + 2, omega=4.0, chi=0.3, J=rng.standard_normal(4 * n * (n + 2)))
+    out.append(("maxwell_vec", mv, rng.standard_normal(mv.n_unknowns), None))
     return out
 
 
-@pytest.mark.parametrize("idx", range(5))
+@pytest.mark.parametrize("idx", range(6))
 def test_taylor_remainder_is_second_order(rng, idx):
     name, p, x, b = _problems(rng)[idx]
     v = rng.standard_normal(x.size)
