@@ -230,7 +230,7 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
   const double* s_sn = sh + 4 * LD;
   __shared__ int s_go;
   __shared__ double s_s2, s_st;
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cj = j - 1;
   const double isig = 1.0 / sigma;
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
