@@ -179,6 +179,36 @@ def _peaks():
         return None
 
 
+class Replicas:
+    """Multi-GPU runs of the benchmark: the path does not shard, so every rank solves its own replica of the
+    workload (weak scaling). The ranks meet at a barrier around the timed region, the job time is the
+    maximum of the ranks' times, and the whole-job rate is all ranks' solves over that time. `dist` is
+    torch.distributed after init_process_group (None: one process); `device` holds the reduction tensor
+    ("cuda" for NCCL, "cpu" for gloo)."""
+
+    def __init__(self, dist=None, device: str = "cpu"):
+        self.dist, self.device = dist, device
+
+    @property
+    def world(self) -> int:
+        return self.dist.get_world_size() if self.dist is not None else 1
+
+    def barrier(self) -> None:
+        if self.dist is not None:
+            self.dist.barrier()
+
+    def max(self, v: float) -> float:
+        if self.dist is None:
+            return v
+        import torch
+        t = torch.tensor([v], dtype=torch.float64, device=self.device)
+        self.dist.all_reduce(t, op=self.dist.ReduceOp.MAX)
+        return float(t.item())
+
+    def rate(self, solves_per_rank: int, max_seconds: float) -> float:
+        return self.world * solves_per_rank / max_seconds
+
+
 def _src_hash() -> str:
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2605_13378_gb300", "csrc")
@@ -535,17 +565,13 @@ def main() -> None:
         import torch.distributed as dist
         dist.init_process_group("nccl")
 
+    replicas = Replicas(dist, "cuda")
+
     def barrier():
-        if dist is not None:
-            dist.barrier()
+        replicas.barrier()
         torch.cuda.synchronize()
 
-    def max_over_ranks(v: float) -> float:
-        if dist is None:
-            return v
-        t = torch.tensor([v], device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        return float(t.item())
+    max_over_ranks = replicas.max
 
     stream = torch.cuda.Stream()
     ctx = J.jfnk_create(local, 0, stream.cuda_stream)
