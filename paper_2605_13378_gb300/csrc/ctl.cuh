@@ -220,19 +220,24 @@ __device__ __forceinline__ void dcgs_stage(GmresCtl* c, int j, double* sh, doubl
   }
 }
 
+// GB300 issues a warp's FP64 instruction over many cycles (two FP64 FMAs per
+// clock per SM), so each scalar is formed once, by one thread, and the
+// rotation chain carries one FMA per step; isig = 1 / sigma comes from the
+// caller, formed while the tail's loads are in flight.
 __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
-                                          double sigma, double g_prev, double target, int m, int active0, int its0) {
+                                          double sigma, double isig, double g_prev, double target, int m,
+                                          int active0, int its0) {
   constexpr int LD = kMaxM + 1;
   double* ss = sh;             // s
   double* zz = sh + LD;        // z
   double* col = sh + 2 * LD;   // column j-1: completed, then rotated
   const double* s_cs = sh + 3 * LD;
   const double* s_sn = sh + 4 * LD;
-  __shared__ int s_go;
-  __shared__ double s_s2, s_st;
+  __shared__ int s_go, s_bad;
+  __shared__ double s_s2, s_st, s_rho, s_irs, s_hn;
+  __shared__ double s_cb[kMaxM + 1], s_sb[kMaxM + 1], s_a[kMaxM + 1];
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
   const int cj = j - 1;
-  const double isig = 1.0 / sigma;
   for (int i = threadIdx.x; i < j; i += blockDim.x) {
     const double si = sigma * S[2 * i];
     ss[i] = si;
@@ -251,18 +256,31 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
     if (lane == 0) s_st = v;
   }
   __syncthreads();
-  // every thread: rho, and the completed (unrotated) column j-1 into hs
-  const double alpha = sigma * sigma * S[2 * j];
-  const double rho2 = alpha - s_s2;
-  const double irs = rho2 > 0.0 ? rsqrt(rho2) : 0.0;   // 1 / rho: one rsqrt for rho and its reciprocal
-  const double rho = rho2 * irs;
-  const bool bad = !finite_d(rho2) || !finite_d(sigma);
-  const double hn = rho * isig;
+  // thread 0: rho (one rsqrt for rho and its reciprocal) and H[j, j-1]
+  if (threadIdx.x == 0) {
+    const double alpha = sigma * sigma * S[2 * j];
+    const double rho2 = alpha - s_s2;
+    const double irs = rho2 > 0.0 ? rsqrt(rho2) : 0.0;
+    s_irs = irs;
+    s_rho = rho2 * irs;
+    s_hn = s_rho * isig;
+    s_bad = !finite_d(rho2) || !finite_d(sigma);
+  }
+  __syncthreads();
+  const double rho = s_rho, irs = s_irs, hn = s_hn;
+  const bool bad = s_bad != 0;
+  // the completed (unrotated) column j-1 into hs, and the products of the
+  // rotation chain that do not depend on the carried entry
   if (j > 0 && !bad) {
     for (int i = threadIdx.x; i < j; i += blockDim.x) hs[(size_t)cj * LD + i] = col[i];
     if (threadIdx.x == 0) {
       hs[(size_t)cj * LD + j] = hn;
       col[j] = hn;
+    }
+    for (int i = threadIdx.x; i < cj; i += blockDim.x) {
+      const double b = (i + 1 < j) ? col[i + 1] : hn;
+      s_cb[i] = s_cs[i] * b;
+      s_sb[i] = s_sn[i] * b;
     }
   }
   __syncthreads();
@@ -279,13 +297,13 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
       } else if (j == 0) {
         c->g[0] = g_prev * rho;      // r = beta rho q_0
       } else {
-        double a = col[0];           // one dependent FMA per rotation on the carried entry
-#pragma unroll 4
+        // the carried entry a_{i+1} = -sn_i a_i + cs_i b_i: one dependent FMA per
+        // rotation (the products cs_i b_i were formed above by all threads); the
+        // rotated entries cs_i a_i + sn_i b_i are formed from s_a afterwards
+        double a = col[0];
         for (int i = 0; i < cj; ++i) {
-          const double b = col[i + 1];
-          const double cb = s_cs[i] * b, sb = s_sn[i] * b;
-          col[i] = fma(s_cs[i], a, sb);
-          a = fma(-s_sn[i], a, cb);
+          s_a[i] = a;
+          a = fma(-s_sn[i], a, s_cb[i]);
         }
         const double f = a, gg = col[cj + 1];
         const double r2 = fma(f, f, gg * gg);     // Hessenberg entries: no overflow in the squares
@@ -336,11 +354,12 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
     }
   }
   __syncthreads();
-  // the completed column j-1 (unrotated and rotated) back to global memory
+  // the completed column j-1 (unrotated and rotated) back to global memory;
+  // rotated entries below the new rotation from the carried entries
   if (j > 0 && !bad)
     for (int i = threadIdx.x; i <= j; i += blockDim.x) {
       c->Hraw[(size_t)cj * LD + i] = hs[(size_t)cj * LD + i];
-      c->H[(size_t)cj * LD + i] = col[i];
+      c->H[(size_t)cj * LD + i] = i < cj ? fma(s_cs[i], s_a[i], s_sb[i]) : col[i];
     }
   if (!s_go) return;
   const double irho = irs;

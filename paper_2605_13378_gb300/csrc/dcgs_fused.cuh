@@ -397,7 +397,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
   const int jj = j + 1;
   __shared__ double Sd[2 * (kMaxM + 1)];
   __shared__ double sh[5 * (kMaxM + 1)];
-  __shared__ double s_ctl[3];
+  __shared__ double s_ctl[4];
   __shared__ int s_m, s_active, s_its;
   const int GB = (int)gridDim.x;
   const size_t ringb = (size_t)S * G.stage_bytes;
@@ -433,6 +433,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
   if (tid == 0) {
     dcgs_after_update(a.ctl, j, Sd[2 * jj]);         // scale[j] = 1, sigma_{j+1} = 1 / ||u_{j+1}||
     s_ctl[0] = a.ctl->scale[jj];
+    s_ctl[3] = 1.0 / s_ctl[0];
     s_ctl[1] = a.ctl->g[j];
     s_ctl[2] = a.ctl->target;
     s_m = a.ctl->m;
@@ -448,7 +449,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
   for (int i = tid; i <= jj; i += blockDim.x) Sd[2 * i + 1] *= sigma;   // dots with J (sigma u_{j+1})
   dcgs_stage(a.ctl, jj, sh, hs);
   __syncthreads();
-  dcgs_step(a.ctl, jj, Sd, has_w, sh, hs, sigma, s_ctl[1], s_ctl[2], s_m, s_active, s_its);
+  dcgs_step(a.ctl, jj, Sd, has_w, sh, hs, sigma, s_ctl[3], s_ctl[1], s_ctl[2], s_m, s_active, s_its);
   __syncthreads();
   if (tid == 0) *a.counter = 0u;
 }

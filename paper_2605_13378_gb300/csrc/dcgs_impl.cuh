@@ -182,7 +182,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   __threadfence();
   __shared__ double S[2 * (kMaxM + 1)];
   __shared__ double sh[5 * (kMaxM + 1)];
-  __shared__ double s_ctl[3];
+  __shared__ double s_ctl[4];
   __shared__ int s_m, s_active, s_its;
   // one round of loads: every block's partials into the drained ring (when
   // they fit beside the completed Hessenberg columns), the control state into
@@ -261,6 +261,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     s_ctl[0] = c0;
     s_ctl[1] = c1;
     s_ctl[2] = c2;
+    s_ctl[3] = 1.0 / c0;
     s_m = cm;
     s_active = cact;
     s_its = cits;
@@ -331,7 +332,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     }
   }
   __syncthreads();
-  dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[1], s_ctl[2], s_m, s_active, s_its);
+  dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[3], s_ctl[1], s_ctl[2], s_m, s_active, s_its);
   __syncthreads();
   if (tid == 0) *counter = 0u;
 }
