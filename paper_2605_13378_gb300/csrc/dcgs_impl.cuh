@@ -183,6 +183,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   __shared__ double S[2 * (kMaxM + 1)];
   __shared__ double sh[5 * (kMaxM + 1)];
   __shared__ double s_ctl[4];
+  __shared__ float s_fhi[2 * (kMaxM + 1)], s_flo[2 * (kMaxM + 1)];
   __shared__ int s_m, s_active, s_its;
   // one round of loads: every block's partials into the drained ring (when
   // they fit beside the completed Hessenberg columns), the control state into
@@ -300,7 +301,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
 #pragma unroll
         for (int u = 0; u < 4; ++u) {
           const int v = v0 + u * nw;
-          if (v < nval) S[v] = (double)sum[u].hi + (double)sum[u].lo;
+          if (v < nval) { s_fhi[v] = sum[u].hi; s_flo[v] = sum[u].lo; }
         }
       }
     } else {
@@ -332,6 +333,12 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     }
   }
   __syncthreads();
+  if constexpr (kFF) {
+    // the float-float sums to FP64, one value per thread (the conversions run on the
+    // FP64 pipe, so they are spread over the block rather than left to lane 0 of each warp)
+    if (tid < nval) S[tid] = (double)s_fhi[tid] + (double)s_flo[tid];
+    __syncthreads();
+  }
   dcgs_step(ctl, j, S, has_w, sh, hs, s_ctl[0], s_ctl[3], s_ctl[1], s_ctl[2], s_m, s_active, s_its);
   __syncthreads();
   if (tid == 0) *counter = 0u;
