@@ -7,9 +7,11 @@
 //           u_{j+1} = dinvr (w - sum_i dc_i q_i - dc_j q_j) (slot j + 1) and
 //           ||u_{j+1}||^2
 // Each reads basis slots 0..j and w once, against three passes of CGS2.
-// Resident form: one super-chunk of every vector involved fills one stage of a
-// two-stage shared-memory ring (bulk copies by producer warp 0, eight
-// consumer warps). Requires n % 8 == 0, like the other streaming passes.
+// Resident form: one super-chunk of every vector involved fills one entry of
+// a shared-memory ring (bulk copies by producer warp 0, eight consumer warps);
+// the ring has as many entries as fit 200 KB, so that short passes keep more
+// than one entry in flight while the consumers read another. Requires
+// n % 8 == 0, like the other streaming passes.
 #pragma once
 
 #include <type_traits>
@@ -18,12 +20,13 @@
 
 namespace jfnk {
 
-constexpr int kDcgsStages = 2;
-constexpr int kDcgsBudget = 100 * 1024;   // bytes per stage
+constexpr int kDcgsRing = 200 * 1024;     // bytes of the ring
+constexpr int kDcgsBudget = 100 * 1024;   // largest entry: two entries always fit
+constexpr int kDcgsMaxStages = 32;
 
 // bytes per vector of a super-chunk holding nv basis slots (+ the w chunk):
-// the largest power of two up to 32 KB whose stage fits the budget, so that
-// passes over few vectors still keep tens of kilobytes in flight per SM
+// the largest power of two up to 32 KB whose entry fits the budget (larger
+// bulk copies stream faster; chunks shrink only as the basis grows)
 template <class TB, class TJ>
 static int dcgs_scb(int nv, bool has_w, int* stage) {
   for (int scb = 32768; scb >= 512; scb >>= 1) {
@@ -35,15 +38,16 @@ static int dcgs_scb(int nv, bool has_w, int* stage) {
   return 0;
 }
 
-// producer: slots 0..nv-1 of super-chunk `it`, then (w not null) the w chunk
+// producer: slots 0..nv-1 of super-chunk `it`, then (w not null) the w chunk,
+// into ring entry it % nst
 template <class TB, class TJ>
 __device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, const TJ* w, int nv, int CE,
-                                             int scb, int stage_bytes, unsigned char* sring, uint64_t* full,
+                                             int scb, int stage_bytes, int nst, unsigned char* sring, uint64_t* full,
                                              uint64_t* empty, unsigned int* err, int* s_abort) {
   const int lane = threadIdx.x & 31;
-  const int sidx = it % kDcgsStages;
-  if (it >= kDcgsStages &&
-      !mbar_wait_bounded(&empty[sidx], (uint32_t)(((it / kDcgsStages) - 1) & 1), kWaitLimitNs)) {
+  const int sidx = it % nst;
+  if (it >= nst &&
+      !mbar_wait_bounded(&empty[sidx], (uint32_t)(((it / nst) - 1) & 1), kWaitLimitNs)) {
     if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); *s_abort = 1; }
     return false;
   }
@@ -63,28 +67,33 @@ __device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, c
   return true;
 }
 
-// Dots pass. Consumer warps 1-4 accumulate q_i . u_j, warps 5-8 q_i . w:
-// each of the 128 threads of a group owns slices sl = t, t + 128, ... of
-// every chunk and keeps one accumulator per basis slot (the form of the
-// other streaming passes: all threads busy whatever j is). The last block to
-// finish sums the block partials and runs dcgs_step.
+// Dots pass. FP32 accumulators and at most 24 basis slots (kJoint): every
+// consumer thread owns slices sl = t, t + 256, ... of every chunk and keeps
+// two accumulators per basis slot, q_i . u_j and q_i . w, so each basis slice
+// is read from shared memory once; the chunks of such passes hold at least
+// 256 slices. Otherwise (FP64 accumulators, or longer bases, whose 2 KB chunks
+// hold 128 slices) warps 1-4 accumulate q_i . u_j and warps 5-8 q_i . w, each
+// of the 128 threads of a group owning slices sl = t, t + 128, ...
+// The last block to finish sums the block partials and runs dcgs_step.
 template <class TB, class TJ, int KMAX>
 __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     k_dcgs_dots(long long n, const TB* __restrict__ V, int j, const TJ* __restrict__ w, GmresCtl* ctl,
-                double* partials, unsigned int* counter, int cap, int scb, int stage_bytes, unsigned int* err) {
+                double* partials, unsigned int* counter, int cap, int scb, int stage_bytes, int nst, unsigned int* err) {
   typedef typename AccS<TJ>::type A;
   constexpr int VW = 16 / (int)sizeof(TB);
   constexpr int NA = KMAX + 1;                 // accumulators: basis slots 0..j, j <= KMAX
-  constexpr int GT = kStreamThreads / 2;       // threads per group
+  constexpr int GT = kStreamThreads / 2;       // threads per group (split form)
+  constexpr bool kJoint = sizeof(A) == 4 && KMAX <= 24;   // chunks of at least 256 slices: every thread busy
+  constexpr int NW = kJoint ? NA : 1;          // w accumulators of the joint form
   if (!ctl->active || (int)gridDim.x > cap) return;   // host sizing error: never write past the partials
   extern __shared__ __align__(128) unsigned char sring[];
-  uint64_t* full = (uint64_t*)(sring + (size_t)kDcgsStages * stage_bytes);
-  uint64_t* empty = full + kDcgsStages;
+  uint64_t* full = (uint64_t*)(sring + (size_t)nst * stage_bytes);
+  uint64_t* empty = full + nst;
   __shared__ int s_abort;
   __shared__ unsigned int s_last;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int q = 0; q < kDcgsStages; ++q) {
+    for (int q = 0; q < nst; ++q) {
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], kStreamThreads / 32);
     }
@@ -97,23 +106,25 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   const int CE = scb / (int)sizeof(TB);
   const long long nsc = (n + CE - 1) / CE;
   const int my = ((long long)blockIdx.x < nsc) ? (int)((nsc - 1 - blockIdx.x) / gridDim.x + 1) : 0;
-  const int role = (warp - 1) >> 2;            // consumers: 0 dots with u_j, 1 dots with w
+  const int role = (warp - 1) >> 2;            // split form: 0 dots with u_j, 1 dots with w
   const int gt = ((warp - 1) & 3) * 32 + lane;
-  A acc[NA];
+  A acc[NA], accw[NW];
 #pragma unroll
   for (int t = 0; t < NA; ++t) acc[t] = A(0);
+#pragma unroll
+  for (int t = 0; t < NW; ++t) accw[t] = A(0);
   if (warp == 0) {
     int it = 0;
     for (; it < my; ++it)
-      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, sring, full, empty, err, &s_abort)) break;
+      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
     if (s_abort && lane == 0) {
-      for (int q = (it - kDcgsStages > 0 ? it - kDcgsStages : 0); q < it; ++q)
-        mbar_wait_bounded(&full[q % kDcgsStages], (uint32_t)((q / kDcgsStages) & 1), kWaitLimitNs);
+      for (int q = (it - nst > 0 ? it - nst : 0); q < it; ++q)
+        mbar_wait_bounded(&full[q % nst], (uint32_t)((q / nst) & 1), kWaitLimitNs);
     }
   } else {
     for (int it = 0; it < my; ++it) {
-      const int sidx = it % kDcgsStages;
-      if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / kDcgsStages) & 1), kWaitLimitNs)) {
+      const int sidx = it % nst;
+      if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / nst) & 1), kWaitLimitNs)) {
         if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); s_abort = 1; }
         break;
       }
@@ -123,7 +134,43 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
       const int cnt = rem < CE ? (int)rem : CE;
       const int nsl = cnt / VW;
       const unsigned char* st = sring + (size_t)sidx * stage_bytes;
-      if (role == 0 || has_w) {
+      if constexpr (kJoint) {
+        const TB* uj = (const TB*)(st + (size_t)j * scb);
+        if (has_w) {
+          const TJ* ws = (const TJ*)(st + (size_t)nv * scb);
+          for (int sl = tid - 32; sl < nsl; sl += kStreamThreads) {
+            A x[VW], y[VW];
+            ld_slice<A, TB, VW>(x, uj + sl * VW);
+            ld_any<A, TJ, VW>(y, ws + sl * VW);
+#pragma unroll
+            for (int t = 0; t < NA; ++t) {
+              if (t <= j) {
+                A q[VW];
+                ld_slice<A, TB, VW>(q, (const TB*)(st + (size_t)t * scb) + sl * VW);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) {
+                  acc[t] += q[e] * x[e];
+                  accw[t] += q[e] * y[e];
+                }
+              }
+            }
+          }
+        } else {
+          for (int sl = tid - 32; sl < nsl; sl += kStreamThreads) {
+            A x[VW];
+            ld_slice<A, TB, VW>(x, uj + sl * VW);
+#pragma unroll
+            for (int t = 0; t < NA; ++t) {
+              if (t <= j) {
+                A q[VW];
+                ld_slice<A, TB, VW>(q, (const TB*)(st + (size_t)t * scb) + sl * VW);
+#pragma unroll
+                for (int e = 0; e < VW; ++e) acc[t] += q[e] * x[e];
+              }
+            }
+          }
+        }
+      } else if (role == 0 || has_w) {
         for (int sl = gt; sl < nsl; sl += GT) {
           A x[VW];
           if (role == 0) ld_slice<A, TB, VW>(x, (const TB*)(st + (size_t)j * scb) + sl * VW);
@@ -145,33 +192,53 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   }
   __syncthreads();
   if (s_abort) return;
-  // block partials: warp butterflies, then the four warps of each group in order
-  __shared__ double red[kStreamThreads / 32][NA];
-  if (warp >= 1) {
+  // block partials: warp butterflies, then the warps in order (all eight in the
+  // joint form, the four of each group in the split form); FP32 partials as
+  // float-float pairs (the cross-block sums then stay in FP32 arithmetic)
+  constexpr bool kFF = std::is_same<A, float>::value;
+  if constexpr (kJoint) {
+    __shared__ float redj[kStreamThreads / 32][2 * NA];
+    if (warp >= 1) {
 #pragma unroll
-    for (int t = 0; t < NA; ++t) {
-      if (t <= j) {
-        const A sv = warp_sum(acc[t]);
-        if (lane == 0) red[warp - 1][t] = (double)sv;
+      for (int t = 0; t < NA; ++t) {
+        if (t <= j) {
+          const float su = warp_sum(acc[t]), sw = warp_sum(accw[t]);
+          if (lane == 0) { redj[warp - 1][2 * t] = su; redj[warp - 1][2 * t + 1] = sw; }
+        }
       }
     }
-  }
-  __syncthreads();
-  // FP32 accumulators: the block partial as a float-float pair (the cross-block
-  // sums then stay in FP32 arithmetic); FP64 accumulators: a double
-  constexpr bool kFF = std::is_same<A, float>::value;
-  for (int v = tid; v < 2 * nv; v += blockDim.x) {
-    const int r = v & 1, t = v >> 1;
-    if constexpr (kFF) {
-      FF sum{(float)red[4 * r][t], 0.0f};
+    __syncthreads();
+    for (int v = tid; v < 2 * nv; v += blockDim.x) {
+      FF sum{redj[0][v], 0.0f};
 #pragma unroll
-      for (int q = 1; q < 4; ++q) sum = ff_add(sum, FF{(float)red[4 * r + q][t], 0.0f});
+      for (int q = 1; q < kStreamThreads / 32; ++q) sum = ff_add(sum, FF{redj[q][v], 0.0f});
       ff_store(&partials[(size_t)blockIdx.x * kMaxK + v], sum);
-    } else {
-      double sum = 0.0;
+    }
+  } else {
+    __shared__ double red[kStreamThreads / 32][NA];
+    if (warp >= 1) {
 #pragma unroll
-      for (int q = 0; q < 4; ++q) sum += red[4 * r + q][t];
-      partials[(size_t)blockIdx.x * kMaxK + v] = sum;
+      for (int t = 0; t < NA; ++t) {
+        if (t <= j) {
+          const A sv = warp_sum(acc[t]);
+          if (lane == 0) red[warp - 1][t] = (double)sv;
+        }
+      }
+    }
+    __syncthreads();
+    for (int v = tid; v < 2 * nv; v += blockDim.x) {
+      const int r = v & 1, t = v >> 1;
+      if constexpr (kFF) {
+        FF sum{(float)red[4 * r][t], 0.0f};
+#pragma unroll
+        for (int q = 1; q < 4; ++q) sum = ff_add(sum, FF{(float)red[4 * r + q][t], 0.0f});
+        ff_store(&partials[(size_t)blockIdx.x * kMaxK + v], sum);
+      } else {
+        double sum = 0.0;
+#pragma unroll
+        for (int q = 0; q < 4; ++q) sum += red[4 * r + q][t];
+        partials[(size_t)blockIdx.x * kMaxK + v] = sum;
+      }
     }
   }
   __threadfence();
@@ -189,7 +256,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   // they fit beside the completed Hessenberg columns), the control state into
   // shared memory
   const int G = (int)gridDim.x, nval = 2 * nv;
-  const size_t ring = (size_t)kDcgsStages * stage_bytes;
+  const size_t ring = (size_t)nst * stage_bytes;
   // partials staged value-major with a padded row, [nval][G + 1], so that the
   // lanes of a warp summing one value read consecutive banks
   const bool staged = ((size_t)(G + 1) * nval + (size_t)j * (kMaxM + 1)) * sizeof(double) <= ring;
@@ -347,19 +414,19 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
 template <class TB, class TJ, int KMAX>
 __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     k_dcgs_update(long long n, TB* __restrict__ V, int j, const TJ* __restrict__ w, GmresCtl* ctl,
-                  RedSite<typename AccS<TJ>::type> red, int scb, int stage_bytes, unsigned int* err) {
+                  RedSite<typename AccS<TJ>::type> red, int scb, int stage_bytes, int nst, unsigned int* err) {
   typedef typename AccS<TJ>::type A;
   constexpr int VW = 16 / (int)sizeof(TB);
   if (!ctl->active) return;
   extern __shared__ __align__(128) unsigned char sring[];
-  uint64_t* full = (uint64_t*)(sring + (size_t)kDcgsStages * stage_bytes);
-  uint64_t* empty = full + kDcgsStages;
+  uint64_t* full = (uint64_t*)(sring + (size_t)nst * stage_bytes);
+  uint64_t* empty = full + nst;
   __shared__ A ca[kMaxM + 1], cc[kMaxM + 1];
   __shared__ A s_gamma, s_cj, s_invr;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   if (tid == 0) {
-    for (int q = 0; q < kDcgsStages; ++q) {
+    for (int q = 0; q < nst; ++q) {
       mbar_init(&full[q], 1);
       mbar_init(&empty[q], kStreamThreads / 32);
     }
@@ -382,16 +449,16 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   if (warp == 0) {
     int it = 0;
     for (; it < my; ++it)
-      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, sring, full, empty, err, &s_abort)) break;
+      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
     if (s_abort && lane == 0) {
-      for (int q = (it - kDcgsStages > 0 ? it - kDcgsStages : 0); q < it; ++q)
-        mbar_wait_bounded(&full[q % kDcgsStages], (uint32_t)((q / kDcgsStages) & 1), kWaitLimitNs);
+      for (int q = (it - nst > 0 ? it - nst : 0); q < it; ++q)
+        mbar_wait_bounded(&full[q % nst], (uint32_t)((q / nst) & 1), kWaitLimitNs);
     }
   } else {
     const A gam = s_gamma, cj = s_cj, invr = s_invr;
     for (int it = 0; it < my; ++it) {
-      const int sidx = it % kDcgsStages;
-      if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / kDcgsStages) & 1), kWaitLimitNs)) {
+      const int sidx = it % nst;
+      if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / nst) & 1), kWaitLimitNs)) {
         if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); s_abort = 1; }
         break;
       }
@@ -448,24 +515,26 @@ static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const vo
   int stage = 0;
   const int scb = dcgs_scb<TB, TJ>(j + 1, w != nullptr, &stage);
   if (scb == 0) return cudaErrorInvalidValue;
-  const size_t smem = (size_t)kDcgsStages * stage + (size_t)kDcgsStages * 16;
+  int nst = kDcgsRing / stage;                          // ring entries, at least two
+  if (nst > kDcgsMaxStages) nst = kDcgsMaxStages;
+  const size_t smem = (size_t)nst * stage + (size_t)nst * 16;
   static bool attr_set[2] = {false, false};
   if (!attr_set[pass - 1]) {
     cudaError_t e = pass == 1 ? cudaFuncSetAttribute(k_dcgs_dots<TB, TJ, KMAX>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     kDcgsStages * kDcgsBudget + 64)
+                                                     kDcgsRing + kDcgsMaxStages * 16)
                               : cudaFuncSetAttribute(k_dcgs_update<TB, TJ, KMAX>,
                                                      cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     kDcgsStages * kDcgsBudget + 64);
+                                                     kDcgsRing + kDcgsMaxStages * 16);
     if (e != cudaSuccess) return e;
     attr_set[pass - 1] = true;
   }
   if (pass == 1)
     k_dcgs_dots<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
-        n, (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb, stage, err);
+        n, (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb, stage, nst, err);
   else
     k_dcgs_update<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
-        n, (TB*)V, j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage, err);
+        n, (TB*)V, j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage, nst, err);
   return cudaGetLastError();
 }
 
@@ -475,6 +544,7 @@ static cudaError_t dcgs_dispatch(int pass, long long n, void* V, int j, const vo
                                  unsigned int* err, int nsm, cudaStream_t st) {
   if (j < 8) return dcgs_launch_k<TB, TJ, 8>(pass, n, V, j, w, ctl, red, err, nsm, st);
   if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st);
+  if (j < 24) return dcgs_launch_k<TB, TJ, 24>(pass, n, V, j, w, ctl, red, err, nsm, st);
   if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st);
   return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st);
 }
