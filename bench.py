@@ -209,11 +209,38 @@ class Replicas:
         return self.world * solves_per_rank / max_seconds
 
 
+def _strip_comments(src: str) -> str:
+    """C/C++/CUDA source without comments and blank runs: what the compiler sees of it."""
+    out, i, n = [], 0, len(src)
+    while i < n:
+        c = src[i]
+        if c in "\"'":                       # string or character literal, kept whole
+            j = i + 1
+            while j < n and src[j] != c:
+                j += 2 if src[j] == "\\" else 1
+            out.append(src[i:j + 1])
+            i = j + 1
+        elif src.startswith("//", i):
+            j = src.find("\n", i)
+            i = n if j < 0 else j
+        elif src.startswith("/*", i):
+            j = src.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def _src_hash() -> str:
+    """Hash of the CUDA sources as compiled (comments and spacing left out), so that stored ncu
+    counters stay tied to the kernels they were taken from and to nothing else."""
     h = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2605_13378_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
-        h.update(open(os.path.join(csrc, f), "rb").read())
+        h.update(f.encode() + b"\0")
+        h.update(_strip_comments(open(os.path.join(csrc, f), encoding="utf-8").read()).encode())
     return h.hexdigest()[:16]
 
 

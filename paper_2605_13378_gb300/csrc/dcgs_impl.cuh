@@ -70,10 +70,11 @@ __device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, c
 // Dots pass. FP32 accumulators and at most 24 basis slots (kJoint): every
 // consumer thread owns slices sl = t, t + 256, ... of every chunk and keeps
 // two accumulators per basis slot, q_i . u_j and q_i . w, so each basis slice
-// is read from shared memory once; the chunks of such passes hold at least
-// 256 slices. Otherwise (FP64 accumulators, or longer bases, whose 2 KB chunks
-// hold 128 slices) warps 1-4 accumulate q_i . u_j and warps 5-8 q_i . w, each
-// of the 128 threads of a group owning slices sl = t, t + 128, ...
+// is read from shared memory once (FP32 bases keep chunks of at least 4 KB,
+// 256 slices, up to 24 slots; a BF16 basis drops to 128 slices at j = 23).
+// Otherwise (FP64 accumulators, or longer bases, whose 2 KB chunks hold 128
+// slices) warps 1-4 accumulate q_i . u_j and warps 5-8 q_i . w, each of the
+// 128 threads of a group owning slices sl = t, t + 128, ...
 // The last block to finish sums the block partials and runs dcgs_step.
 template <class TB, class TJ, int KMAX>
 __global__ void __launch_bounds__(kStreamThreads + 32, 1)

@@ -1,4 +1,5 @@
-"""Host logic of the benchmark suite (CPU only): the paper's failure rule and Dolan-More profiles.
+"""Host logic of the benchmark suite (CPU only): the paper's failure rule and Dolan-More profiles,
+and the source hash that ties stored ncu counters to the kernels they were taken from.
 
 Sec. 4 (metrics and failure criteria): a time-dependent run fails when it
 stops early or when more than 20% of its steps miss 100 x tol_Newton;
@@ -34,3 +35,25 @@ def test_performance_profile_by_hand():
     for s in pr.values():
         assert all(x <= y for x, y in zip(s["rho"], s["rho"][1:]))
         assert math.isclose(s["rho"][-1], s["completion"])
+
+
+def test_strip_comments_keeps_code_and_literals():
+    src = 'int a = 1; // line\n/* block\n  comment */ const char* s = "a//b/*c*/"; char c = \'/\';\n\n  float d;'
+    assert bench._strip_comments(src) == 'int a = 1; const char* s = "a//b/*c*/"; char c = \'/\'; float d;'
+    assert bench._strip_comments('x = "q\\"//"; // tail') == 'x = "q\\"//";'
+
+
+def test_src_hash_follows_code_not_comments(tmp_path, monkeypatch):
+    csrc = tmp_path / "paper_2605_13378_gb300" / "csrc"
+    csrc.mkdir(parents=True)
+    k = csrc / "k.cu"
+    k.write_text("__global__ void k(float* x) { x[0] = 1.0f; }\n")
+    monkeypatch.setattr(bench, "ROOT", str(tmp_path))
+    h0 = bench._src_hash()
+    k.write_text("// a kernel\n__global__ void k(float* x) {\n  x[0] = 1.0f;   /* one */\n}\n")
+    assert bench._src_hash() == h0
+    k.write_text("__global__ void k(float* x) { x[0] = 2.0f; }\n")
+    assert bench._src_hash() != h0
+    k.write_text("__global__ void k(float* x) { x[0] = 1.0f; }\n")
+    (csrc / "extra.cuh").write_text("")
+    assert bench._src_hash() != h0          # a new file counts, even an empty one
