@@ -28,6 +28,7 @@ import argparse
 import hashlib
 import json
 import math
+import re
 
 import numpy as np
 import os
@@ -210,14 +211,22 @@ class Replicas:
 
 
 def _strip_comments(src: str) -> str:
-    """C/C++/CUDA source without comments and blank runs: what the compiler sees of it."""
-    out, i, n = [], 0, len(src)
+    """C/C++/CUDA source without comments, runs of white space outside literals collapsed to one space:
+    what the compiler sees of it. String and character literals are kept byte for byte."""
+    out, code, i, n = [], [], 0, len(src)
+
+    def flush():
+        if code:
+            out.append(re.sub(r"\s+", " ", "".join(code)))
+            code.clear()
+
     while i < n:
         c = src[i]
         if c in "\"'":                       # string or character literal, kept whole
             j = i + 1
             while j < n and src[j] != c:
                 j += 2 if src[j] == "\\" else 1
+            flush()
             out.append(src[i:j + 1])
             i = j + 1
         elif src.startswith("//", i):
@@ -226,17 +235,20 @@ def _strip_comments(src: str) -> str:
         elif src.startswith("/*", i):
             j = src.find("*/", i + 2)
             i = n if j < 0 else j + 2
-            out.append(" ")
+            code.append(" ")
         else:
-            out.append(c)
+            code.append(c)
             i += 1
-    return " ".join("".join(out).split())
+    flush()
+    return "".join(out).strip()
 
 
 def _src_hash() -> str:
-    """Hash of the CUDA sources as compiled (comments and spacing left out), so that stored ncu
-    counters stay tied to the kernels they were taken from and to nothing else."""
+    """Hash of the CUDA sources as compiled (comments and spacing left out) and of the nvcc architecture and
+    flags they are built with, so that stored ncu counters stay tied to the kernels they were taken from."""
+    from paper_2605_13378_gb300 import build as B
     h = hashlib.sha256()
+    h.update(" ".join(B.ARCH + [f for f in B.FLAGS if not f.startswith("-I")]).encode() + b"\0")
     csrc = os.path.join(ROOT, "paper_2605_13378_gb300", "csrc")
     for f in sorted(os.listdir(csrc)):
         h.update(f.encode() + b"\0")

@@ -36,7 +36,7 @@
 extern "C" {
 #endif
 
-#define JFNK_ABI_VERSION 1
+#define JFNK_ABI_VERSION 2
 #define JFNK_MAX_RESTART 64   /* largest GMRES restart length m */
 
 typedef struct jfnk_ctx jfnk_ctx;
@@ -100,7 +100,14 @@ typedef enum { JFNK_EPS_SCALED = 0, JFNK_EPS_PAPER = 1 } jfnk_fd_rule;
  * arithmetic; each cycle that converges before its last column applies the
  * Jacobian once more. DCGS2 runs on the streaming kernels: N (all fields) a
  * multiple of 8, else JFNK_E_INVALID. The batched entry points use CGS2. */
-typedef enum { JFNK_CGS2 = 0, JFNK_DCGS2 = 1 } jfnk_ortho;
+/* JFNK_DCGS2_FUSED is delayed CGS2 with the update of step j, the AD JVP of
+ * the next candidate and the dots of step j + 1 in one kernel, so the basis
+ * is read once per step instead of twice. It needs lin = JFNK_AD, prec =
+ * JFNK_FP32 or JFNK_MIXED_FP32 and a 2D problem with face neighbours only
+ * (Allen-Cahn, Maxwell TE, 2D Burgers) whose rows fit its shared-memory plan
+ * (JFNK_E_INVALID otherwise). It gives the iterates of JFNK_DCGS2 but is
+ * slower on GB300, being bound by instruction issue rather than HBM. */
+typedef enum { JFNK_CGS2 = 0, JFNK_DCGS2 = 1, JFNK_DCGS2_FUSED = 2 } jfnk_ortho;
 
 /* One nonlinear problem: PDE, grid and time step (App. A and the benchmark
  * variants). The implicit step is the theta-method residual
@@ -143,6 +150,9 @@ typedef struct {
   double res_final;     /* final ||F|| of the last solve */
   double ms;            /* host wall time of the call */
   double dt_last;       /* time step of the last implicit step (the CFL step when adaptive) */
+  double ls_alpha[16];  /* jfnk_solve: the step alpha the line search accepted in each of the
+                           first 16 Newton iterations of the last nonlinear solve (0: none);
+                           the batched and served paths leave it 0 */
 } jfnk_report;
 
 /* Defaults of the paper for a precision (Sec. 3.3): tol_Newton 1e-6 / 1e-4,
@@ -166,23 +176,34 @@ jfnk_status jfnk_set_problem(jfnk_ctx* ctx, const jfnk_problem* prob);
  * lin = JFNK_AD: one dual-number sweep gives F(x) (written to F_out when it
  * is not NULL) and J(x) v (Eq. 9). lin = JFNK_FD: (F(x + eps v) - F(x))/eps
  * (Eq. 7) with eps = fd_eps when fd_eps > 0, else the scaled rule
- * sqrt(eps_mach)(1 + ||x||)/||v|| (both norms reduced on the device; v = 0
- * is JFNK_E_INVALID through a non-finite step). prec = JFNK_FP64: x, v, b,
- * F_out, Jv_out are double; JFNK_FP32: float. b is the constant part of the
- * theta-method residual (NULL: zero). All pointers are device pointers; the
- * call is stream-ordered and returns after the work is queued. */
+ * sqrt(eps_mach)(1 + ||x||)/||v|| (both norms reduced on the device; for
+ * v = 0 the rule takes ||v|| = 1, so the step stays finite and the quotient
+ * is zero up to the rounding of F(x) between the two sweeps). prec =
+ * JFNK_FP64: x, v, b, F_out, Jv_out are double; JFNK_FP32: float. b is the
+ * constant part of the theta-method residual (NULL: zero). All pointers are
+ * device pointers; the call is stream-ordered and returns after the work is
+ * queued. A 2D Burgers problem with an adaptive step is refused as in
+ * jfnk_residual. */
 jfnk_status jfnk_jvp(jfnk_ctx* ctx, int lin, int prec, const void* x, const void* v,
                      const void* b, void* F_out, void* Jv_out, double fd_eps);
 
 /* Residual of the installed problem: F_out = F(x; b) in precision prec
- * (device pointers, stream-ordered). */
+ * (device pointers, stream-ordered). A 2D Burgers problem with an adaptive
+ * step (Courant number p[2] > 0) has no time step outside jfnk_solve:
+ * JFNK_E_INVALID (install it with p[2] = 0 and the step as dt). */
 jfnk_status jfnk_residual(jfnk_ctx* ctx, int prec, const void* x, const void* b, void* F_out);
 
 /* Solve `steps` implicit steps from x_prev (NULL: from x_inout), writing the
  * final state to x_inout; for the Maxwell problem one nonlinear solve from
  * x_inout (or the Born start). x_prev and x_inout are FP64, host or device.
- * Synchronous. Returns JFNK_OK when every step converged, otherwise the
- * status of the first failing step; rep (host, may be NULL) gets counts. */
+ * The backtracking line search of each Newton step is decided on the device:
+ * the trial residuals F(x + alpha d) for alpha = 1, 1/2, ... down to
+ * ls_min_alpha are queued together, the last block of each trial applies the
+ * Armijo test and either accepts it or halves alpha for the next, and the
+ * trials after the accepted one do nothing; the host reads the result back
+ * once per Newton step. Synchronous. Returns JFNK_OK when every step
+ * converged, otherwise the status of the first failing step; rep (host, may
+ * be NULL) gets counts. */
 jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_prev,
                        double* x_inout, int steps, jfnk_report* rep);
 
@@ -267,8 +288,13 @@ void jfnk_reset_stats(jfnk_ctx* ctx);
  * Errors: JFNK_E_INVALID for bad arguments, JFNK_E_OOM as above,
  * JFNK_E_CUDA when a launch fails. Stream-ordered; returns once queued.
  * The first call on each device looks the scratch array's address up for
- * that device (with it current); make that first call before capturing the
- * stream. Every call reuses the same array and clears the part that must
+ * that device (with it current) and keeps it for the life of the process;
+ * make that first call before capturing the stream. A device reset
+ * (cudaDeviceReset) unloads the array, and the kept address is then stale:
+ * do not call this entry point on a device after resetting it. For v = 0 the
+ * step rule takes ||v|| = 1, as in jfnk_jvp. A 2D Burgers
+ * problem with an adaptive step (p[2] > 0) is JFNK_E_INVALID, as for
+ * jfnk_jvp. Every call reuses the same array and clears the part that must
  * start at zero, so calls that overlap on the GPU (other streams, other host
  * threads) race on it: serialise them. */
 #define JFNK_NOALLOC_MAX_FX_BYTES 4194304u

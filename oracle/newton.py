@@ -61,6 +61,7 @@ class Report:
     res0: float = 0.0
     res_final: float = 0.0
     history: list = field(default_factory=list)
+    alphas: list = field(default_factory=list)   # accepted line-search step of each Newton iteration
 
 
 def _operator(problem, b, x, Fx, opt: Options, rep: Report):
@@ -159,6 +160,7 @@ def newton(problem, b, x0: np.ndarray, opt: Options, denom: float | None = None)
             alpha *= 0.5
             rep.ls_backtracks += 1
         x, F, fnorm = xt, Ft, ft
+        rep.alphas.append(alpha)
         rep.newton_its += 1
         rep.history.append(fnorm)
     rep.res_final = fnorm

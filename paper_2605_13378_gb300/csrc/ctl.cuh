@@ -49,6 +49,42 @@ struct BicgCtl {
   volatile int* host_active;       // mapped host word mirroring `active` (may be null)
 };
 
+// Backtracking line search of one Newton step (Sec. 2, after Eq. 4), decided
+// on the device. The host queues the trial residuals F(x + alpha d) for
+// alpha = 1, 1/2, ... down to the smallest trial at once; the last block of
+// each trial applies the Armijo test to its ||F|| and either accepts the
+// trial (done = 1: the trials queued after it return at once, so the trial
+// buffers keep the accepted state) or halves alpha for the next one. The
+// smallest trial is accepted when no trial passes (a line-search failure).
+struct LsCtl {
+  double fnorm;       // ||F(x_k)||, the merit of the current iterate
+  double alpha;       // step of the next trial
+  double c1, min_alpha;
+  double ft;          // ||F(x_k + alpha d)|| of the accepted trial
+  double alpha_acc;   // the accepted step
+  int done;           // a trial has been accepted
+  int backtracks;     // halvings in this Newton step
+  int failures;       // 1 when the smallest trial was taken without passing
+  int accept_first;   // take the first trial as it is (the linear Born solve)
+};
+
+__device__ __forceinline__ void ls_decide(LsCtl* c, double f2) {
+  const double ft = sqrt(f2), a = c->alpha;
+  bool accept = c->accept_first || (isfinite(ft) && ft <= (1.0 - c->c1 * a) * c->fnorm);
+  if (!accept && a * 0.5 < c->min_alpha) {
+    accept = true;
+    c->failures = 1;
+  }
+  if (accept) {
+    c->ft = ft;
+    c->alpha_acc = a;
+    c->done = 1;
+  } else {
+    c->alpha = a * 0.5;
+    c->backtracks += 1;
+  }
+}
+
 __device__ __forceinline__ void mirror_active(volatile int* h, int a) {
   if (h) {
     *h = a;

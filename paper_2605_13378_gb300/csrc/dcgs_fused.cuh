@@ -34,7 +34,7 @@
 // streaming passes. On GB300 that makes it issue- and latency-bound (about
 // 1.4 TB/s of its own algorithmic bytes on the 2048^2 Allen-Cahn workload,
 // against 3.8 and 5.5 TB/s for the dots and update passes), so it is
-// selected only on request (JFNK_FUSED=1).
+// selected only on request (opts.ortho = JFNK_DCGS2_FUSED).
 #pragma once
 
 #include "dcgs_impl.cuh"
@@ -238,8 +238,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
     }
     if (!ok && lane == 0) {
       // drain the copies still in flight (bounded) before the CTA leaves
+      const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (idx - S > 0 ? idx - S : 0); q < idx; ++q)
-        mbar_wait_bounded(&full[q % S], (uint32_t)((q / S) & 1), kWaitLimitNs);
+        mbar_wait_until(&full[q % S], (uint32_t)((q / S) & 1), deadline);
     }
   } else {
     // ---- consumers, one column position each. Step k (rows ra - 1 .. rb,
@@ -456,13 +457,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
 
 template <class PDE, int KMAX>
 static cudaError_t dcgs_fused_k(const FusedArgs& a, const ProbDev& P, cudaStream_t st) {
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_dcgs_fused<PDE, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kFusedBudget);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static SmemOptIn opt_in;
+  cudaError_t e = smem_opt_in(k_dcgs_fused<PDE, KMAX>, opt_in, kFusedBudget);
+  if (e != cudaSuccess) return e;
   k_dcgs_fused<PDE, KMAX><<<a.g.grid, kStreamThreads + 32, a.g.smem, st>>>(a, P);
   return cudaGetLastError();
 }

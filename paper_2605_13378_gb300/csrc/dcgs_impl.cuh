@@ -119,8 +119,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     for (; it < my; ++it)
       if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
     if (s_abort && lane == 0) {
+      const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (it - nst > 0 ? it - nst : 0); q < it; ++q)
-        mbar_wait_bounded(&full[q % nst], (uint32_t)((q / nst) & 1), kWaitLimitNs);
+        mbar_wait_until(&full[q % nst], (uint32_t)((q / nst) & 1), deadline);
     }
   } else {
     for (int it = 0; it < my; ++it) {
@@ -452,8 +453,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     for (; it < my; ++it)
       if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
     if (s_abort && lane == 0) {
+      const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (it - nst > 0 ? it - nst : 0); q < it; ++q)
-        mbar_wait_bounded(&full[q % nst], (uint32_t)((q / nst) & 1), kWaitLimitNs);
+        mbar_wait_until(&full[q % nst], (uint32_t)((q / nst) & 1), deadline);
     }
   } else {
     const A gam = s_gamma, cj = s_cj, invr = s_invr;
@@ -519,17 +521,10 @@ static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const vo
   int nst = kDcgsRing / stage;                          // ring entries, at least two
   if (nst > kDcgsMaxStages) nst = kDcgsMaxStages;
   const size_t smem = (size_t)nst * stage + (size_t)nst * 16;
-  static bool attr_set[2] = {false, false};
-  if (!attr_set[pass - 1]) {
-    cudaError_t e = pass == 1 ? cudaFuncSetAttribute(k_dcgs_dots<TB, TJ, KMAX>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     kDcgsRing + kDcgsMaxStages * 16)
-                              : cudaFuncSetAttribute(k_dcgs_update<TB, TJ, KMAX>,
-                                                     cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                                     kDcgsRing + kDcgsMaxStages * 16);
-    if (e != cudaSuccess) return e;
-    attr_set[pass - 1] = true;
-  }
+  static SmemOptIn opt_in[2];
+  cudaError_t e = pass == 1 ? smem_opt_in(k_dcgs_dots<TB, TJ, KMAX>, opt_in[0], kDcgsRing + kDcgsMaxStages * 16)
+                            : smem_opt_in(k_dcgs_update<TB, TJ, KMAX>, opt_in[1], kDcgsRing + kDcgsMaxStages * 16);
+  if (e != cudaSuccess) return e;
   if (pass == 1)
     k_dcgs_dots<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
         n, (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb, stage, nst, err);

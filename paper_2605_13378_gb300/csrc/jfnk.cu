@@ -91,6 +91,7 @@ struct jfnk_ctx {
   bool stream_ok = true;          // bulk-copy streaming of the basis allowed (JFNK_NO_STREAM=1 disables)
   GmresCtl* gctl = nullptr;
   BicgCtl* bctl = nullptr;
+  LsCtl* lsc = nullptr;           // line search of the current Newton step
   RedWs red{};
   int red_cap_blocks = 0;
   // pinned / mapped host memory
@@ -267,11 +268,12 @@ struct Solver {
   double aux_bytes(int tcode) const { return (P.pde == 3 && P.eps64) ? (double)P.ncell * vt_size(tcode) : 0.0; }
 
   jfnk_status residual(const void* xx, const void* dd, double alpha, void* Fo, void* xo, void* x32o, double* sums,
-                       int tcode, const void* bb) {
+                       int tcode, const void* bb, LsCtl* ls = nullptr, int tag = -1) {
     double bytes = (double)N * vt_size(tcode) * (1 + (dd ? 1 : 0) + (bb ? 1 : 0) + (Fo ? 1 : 0) + (xo ? 1 : 0)) +
                    (x32o ? (double)N * 4 : 0.0) + aux_bytes(tcode);
-    int ev = tm_begin(ctx, KC_RESIDUAL, bytes, -1);
-    cudaError_t e = launch_residual(P, tcode, xx, dd, alpha, bb, Fo, xo, (float*)x32o, ctx->red, sums, ctx->stream);
+    int ev = tm_begin(ctx, KC_RESIDUAL, bytes, tag);
+    cudaError_t e = launch_residual(P, tcode, xx, dd, alpha, bb, Fo, xo, (float*)x32o, ctx->red, sums, ctx->stream,
+                                    ls);
     tm_end(ctx, ev);
     if (e != cudaSuccess) return cuda_fail(ctx, e, "residual kernel");
     return JFNK_OK;
@@ -279,6 +281,7 @@ struct Solver {
 
   jfnk_status jvp(JvpArgs& a, int tag) {
     a.t = tj;
+    a.err = ctx->derr;
     const double s = (double)sj();
     double bytes = (double)N * (s + vt_size(a.tv) + s) + aux_bytes(tj);     // x, v -> out
     if (a.lin == 1) bytes += (double)N * s;                                 // F(x)
@@ -385,15 +388,10 @@ struct Solver {
   // u_{j+1} and the dots of step j + 1 in one kernel; the pass of step m - 1
   // takes the dots of u_m without a JVP and so completes the last column.
   // Candidates alternate between two buffers, and so do the JVP outputs.
-  // Opt-in (JFNK_FUSED=1): it reads the basis once per step instead of
-  // twice, but with one column per thread per row it is bound by instruction
-  // issue and latency, and the two streaming passes are faster on GB300.
-  bool fused_on(int m) const {
-    const char* env = std::getenv("JFNK_FUSED");   // 1: the fused pass (measured slower than two passes)
-    return env && env[0] == '1' && o.lin == JFNK_AD && o.ortho == JFNK_DCGS2 && tb == VT_F32 && tj == VT_F32 && ctx->stream_ok &&
-           ctx->ws.u2[0] && dcgs_fused_supported(P, m, ctx->nsm);
-  }
-
+  // Chosen by opts.ortho = JFNK_DCGS2_FUSED (validate_opts checks that it
+  // applies): it reads the basis once per step instead of twice, but with one
+  // column per thread per row it is bound by instruction issue and latency,
+  // and the two streaming passes are faster on GB300.
   jfnk_status dcgs_cycle_fused(int m, int* steps_run) {
     jfnk_ctx::Ws& w = ctx->ws;
     const double nv = (double)N;
@@ -442,7 +440,7 @@ struct Solver {
     const int m = o.restart;
     const double nv = (double)N;
     const bool streamed = ctx->stream_ok && stream_supported(N);
-    const bool fused = o.ortho == JFNK_DCGS2 && fused_on(m);
+    const bool fused = o.ortho == JFNK_DCGS2_FUSED;
     *ctx->hflag = 1;   // before any launch that may clear it
     int ev = tm_begin(ctx, KC_GINIT, nv * (ss() + sb() + sj() + ss()), -1);
     cudaError_t e = launch_gmres_init(ts, tj, tb, td, N, F, w.V, w.rhsk, w.d, ctx->gctl, sc, o.tol_krylov, m,
@@ -486,7 +484,7 @@ struct Solver {
           if (s) return s;
         }
       }
-      if (o.ortho == JFNK_DCGS2) {
+      if (o.ortho == JFNK_DCGS2 || o.ortho == JFNK_DCGS2_FUSED) {
         int steps_run = 0;
         jfnk_status s = fused ? dcgs_cycle_fused(m, &steps_run) : dcgs_cycle(m, &steps_run);
         if (s) return s;
@@ -694,6 +692,8 @@ struct Solver {
     double fnorm = std::sqrt(ctx->hbuf[0]);
     const double f0 = denom > 0 ? denom : fnorm;
     rep.res0 = f0;
+    for (double& a : rep.ls_alpha) a = 0.0;
+    int nits = 0;   // Newton iterations of this solve
     *nstatus = JFNK_OK;
     for (int k = 0; k <= o.max_newton; ++k) {
       if (!std::isfinite(fnorm)) { *nstatus = JFNK_E_NONFINITE; break; }
@@ -709,20 +709,33 @@ struct Solver {
       if (s) return s;
       if (kst == JFNK_E_BREAKDOWN || kst == JFNK_E_NONFINITE) { *nstatus = kst; break; }
       if (kst == JFNK_E_NOT_CONVERGED) rep.krylov_failures += 1;
-      // backtracking line search on ||F|| (the linear Born solve takes the full step)
-      double alpha = 1.0, ft = 0.0;
-      for (;;) {
-        s = residual(x, w.d, alpha, Ft, xt, tj != ts ? x32t : nullptr, st, ts, bb);
+      // backtracking line search on ||F||, decided on the device (LsCtl): every trial
+      // alpha = 1, 1/2, ..., down to the smallest is queued at once, the last block of
+      // each trial takes the Armijo decision, and the trials after the accepted one do
+      // nothing, so Ft, xt and st hold the accepted state. One read-back per Newton
+      // step. The linear Born solve takes the full step.
+      int ntrial = 1;
+      if (!linear_once)
+        for (double a = 1.0; a * 0.5 >= o.ls_min_alpha; a *= 0.5) ++ntrial;
+      cudaError_t e = launch_ls_begin(ctx->lsc, fnorm, o.ls_c1, o.ls_min_alpha, linear_once ? 1 : 0, ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "line search");
+      for (int q = 0; q < ntrial; ++q) {
+        s = residual(x, w.d, 1.0, Ft, xt, tj != ts ? x32t : nullptr, st, ts, bb, ctx->lsc, q);
         if (s) return s;
-        s = sync_read(st, 16);
-        if (s) return s;
-        ft = std::sqrt(ctx->hbuf[0]);
-        if (linear_once) break;
-        if (std::isfinite(ft) && ft <= (1.0 - o.ls_c1 * alpha) * fnorm) break;
-        if (alpha * 0.5 < o.ls_min_alpha) { rep.ls_failures += 1; break; }
-        alpha *= 0.5;
-        rep.ls_backtracks += 1;
       }
+      CK(cudaMemcpyAsync((char*)ctx->hbuf + 4096, ctx->lsc, sizeof(LsCtl), cudaMemcpyDeviceToHost, ctx->stream),
+         "read-back");
+      s = sync_read(st, 16);
+      if (s) return s;
+      LsCtl ls;
+      std::memcpy(&ls, (char*)ctx->hbuf + 4096, sizeof(LsCtl));
+      tm_harvest(ctx, ls.backtracks + 1, -1.0);
+      if (!ls.done) return fail(ctx, JFNK_E_CUDA, "line search: no trial was accepted");
+      const double ft = ls.ft;
+      rep.ls_backtracks += ls.backtracks;
+      rep.ls_failures += ls.failures;
+      if (nits < 16) rep.ls_alpha[nits] = ls.alpha_acc;
+      ++nits;
       std::swap(x, xt); std::swap(F, Ft); std::swap(sc, st); std::swap(x32, x32t);
       fnorm = ft;
       rep.newton_its += 1;
@@ -767,6 +780,7 @@ static jfnk_status jfnk_create_impl(jfnk_ctx* ctx, int device, size_t hbm_budget
   if ((s = dalloc(ctx, (void**)&ctx->dsc, 64 * sizeof(double), nullptr)) ||
       (s = dalloc(ctx, (void**)&ctx->gctl, sizeof(GmresCtl), nullptr)) ||
       (s = dalloc(ctx, (void**)&ctx->bctl, sizeof(BicgCtl), nullptr)) ||
+      (s = dalloc(ctx, (void**)&ctx->lsc, sizeof(LsCtl), nullptr)) ||
       (s = dalloc(ctx, (void**)&ctx->red.counter, 256, nullptr)) ||
       (s = dalloc(ctx, (void**)&ctx->derr, 256, nullptr)))
     return s;
@@ -857,7 +871,7 @@ void jfnk_destroy(jfnk_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   ws_free(ctx);
   cudaFree(ctx->eps64); cudaFree(ctx->eps32); cudaFree(ctx->src64); cudaFree(ctx->src32);
-  cudaFree(ctx->dsc); cudaFree(ctx->gctl); cudaFree(ctx->bctl);
+  cudaFree(ctx->dsc); cudaFree(ctx->gctl); cudaFree(ctx->bctl); cudaFree(ctx->lsc);
   cudaFree(ctx->red.partials); cudaFree(ctx->red.counter); cudaFree(ctx->jscratch); cudaFree(ctx->derr);
   if (ctx->hflag) cudaFreeHost((void*)ctx->hflag);
   if (ctx->hbuf) cudaFreeHost(ctx->hbuf);
@@ -910,6 +924,9 @@ jfnk_status jfnk_residual(jfnk_ctx* ctx, int prec, const void* x, const void* b,
   if (!ctx || !x || !F) return JFNK_E_INVALID;
   if (!ctx->have_prob) return fail(ctx, JFNK_E_INVALID, "no problem set");
   if (prec != JFNK_FP64 && prec != JFNK_FP32) return fail(ctx, JFNK_E_INVALID, "prec must be FP64 or FP32");
+  if (ctx->P.cfl > 0.0)
+    return fail(ctx, JFNK_E_INVALID, "adaptive time step (Courant number > 0): the step exists only inside "
+                                     "jfnk_solve; install the problem with C = 0 and dt");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   cudaError_t e = launch_residual(ctx->P, prec == JFNK_FP64 ? VT_F64 : VT_F32, x, nullptr, 0.0,
                                   ctx->P.bvp ? nullptr : b, F, nullptr, nullptr, ctx->red, nullptr, ctx->stream);
@@ -923,6 +940,9 @@ jfnk_status jfnk_jvp(jfnk_ctx* ctx, int lin, int prec, const void* x, const void
   if (!ctx->have_prob) return fail(ctx, JFNK_E_INVALID, "no problem set");
   if (lin != JFNK_AD && lin != JFNK_FD) return fail(ctx, JFNK_E_INVALID, "lin must be AD or FD");
   if (prec != JFNK_FP64 && prec != JFNK_FP32) return fail(ctx, JFNK_E_INVALID, "prec must be FP64 or FP32");
+  if (ctx->P.cfl > 0.0)
+    return fail(ctx, JFNK_E_INVALID, "adaptive time step (Courant number > 0): the step exists only inside "
+                                     "jfnk_solve; install the problem with C = 0 and dt");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   const int t = prec == JFNK_FP64 ? VT_F64 : VT_F32;
   const long long N = ctx->N;
@@ -930,6 +950,7 @@ jfnk_status jfnk_jvp(jfnk_ctx* ctx, int lin, int prec, const void* x, const void
   JvpArgs a;
   std::memset(&a, 0, sizeof(a));
   a.lin = lin; a.t = t; a.tv = t; a.x = x; a.v = v; a.b = b; a.out = Jv_out; a.c_jv = 1.0;
+  a.err = ctx->derr;
   if (lin == JFNK_AD) {
     a.F = F_out;
   } else {
@@ -981,9 +1002,17 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
   if (!(o->tol_newton >= 0) || !(o->tol_krylov >= 0)) return fail(ctx, JFNK_E_INVALID, "bad tolerances");
   if (!(o->ls_min_alpha > 0.0 && o->ls_min_alpha <= 1.0)) return fail(ctx, JFNK_E_INVALID, "bad ls_min_alpha");
   if (o->fd_rule != JFNK_EPS_SCALED && o->fd_rule != JFNK_EPS_PAPER) return fail(ctx, JFNK_E_INVALID, "bad fd_rule");
-  if (o->ortho != JFNK_CGS2 && o->ortho != JFNK_DCGS2) return fail(ctx, JFNK_E_INVALID, "bad ortho");
-  if (o->krylov == JFNK_GMRES && o->ortho == JFNK_DCGS2 && !(ctx->stream_ok && stream_supported(ctx->N)))
+  if (o->ortho != JFNK_CGS2 && o->ortho != JFNK_DCGS2 && o->ortho != JFNK_DCGS2_FUSED)
+    return fail(ctx, JFNK_E_INVALID, "bad ortho");
+  if (o->krylov == JFNK_GMRES && o->ortho != JFNK_CGS2 && !(ctx->stream_ok && stream_supported(ctx->N)))
     return fail(ctx, JFNK_E_INVALID, "delayed CGS2 needs the streaming kernels (unknowns a multiple of 8)");
+  if (o->krylov == JFNK_GMRES && o->ortho == JFNK_DCGS2_FUSED) {
+    const bool ok = o->lin == JFNK_AD && tb == VT_F32 && tj == VT_F32 && ctx->stream_ok &&
+                    dcgs_fused_supported(ctx->P, o->restart, ctx->nsm);
+    if (!ok)
+      return fail(ctx, JFNK_E_INVALID, "the one-pass delayed CGS2 form needs the AD JVP, FP32 JVP and basis, and a "
+                                       "2D problem with face neighbours only whose rows fit its shared-memory plan");
+  }
   return JFNK_OK;
 }
 

@@ -48,12 +48,15 @@ StencilGeom stencil_geom(const ProbDev& P);
 // null); on failure *why (may be null) says what is wrong.
 bool make_probdev(const jfnk_problem* pr, ProbDev* P, std::string* why);
 
+struct LsCtl;
 // F = F(x + alpha d; b) in precision t (x, d, b, F, xout of type t; d, b,
 // F, xout, x32 may be null). sums[0] = ||F||^2, sums[1] = ||x + alpha d||^2
-// (double) when sums != null.
+// (double) when sums != null. With ls (and sums) not null the launch is a
+// line-search trial: alpha is ls->alpha, the kernel does nothing once
+// ls->done is set, and its last block applies the Armijo decision (LsCtl).
 cudaError_t launch_residual(const ProbDev& P, int t, const void* x, const void* d, double alpha,
                             const void* b, void* F, void* xout, float* x32, RedWs red, double* sums,
-                            cudaStream_t st);
+                            cudaStream_t st, LsCtl* ls = nullptr);
 
 // b = M(xn) + (1 - theta) dt G(xn) in precision t.
 cudaError_t launch_rhs(const ProbDev& P, int t, const void* xn, void* b, cudaStream_t st);
@@ -79,6 +82,7 @@ struct JvpArgs {
   double eps_fixed; int eps_rule; const double* xn2; const double* vn2;
   float* eps_out;              // FD: the step used (for reporting), may be null
   const int* active;           // device flag: the kernel does nothing when *active == 0 (null: always run)
+  unsigned int* err;           // device error word for bounded waits of the staged sweep (null: not staged)
 };
 cudaError_t launch_jvp(const ProbDev& P, const JvpArgs& a, RedWs red, cudaStream_t st);
 

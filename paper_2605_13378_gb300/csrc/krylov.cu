@@ -441,6 +441,25 @@ cudaError_t launch_gmres_finish(int tb, int td, long long n, const void* V, void
   return cudaGetLastError();
 }
 
+// Start of the line search of one Newton step: trial alpha = 1 from the merit fnorm = ||F(x_k)||.
+__global__ void k_ls_begin(LsCtl* c, double fnorm, double c1, double min_alpha, int accept_first) {
+  c->fnorm = fnorm;
+  c->alpha = 1.0;
+  c->c1 = c1;
+  c->min_alpha = min_alpha;
+  c->ft = 0.0;
+  c->alpha_acc = 0.0;
+  c->done = 0;
+  c->backtracks = 0;
+  c->failures = 0;
+  c->accept_first = accept_first;
+}
+
+cudaError_t launch_ls_begin(LsCtl* c, double fnorm, double c1, double min_alpha, int accept_first, cudaStream_t st) {
+  k_ls_begin<<<1, 1, 0, st>>>(c, fnorm, c1, min_alpha, accept_first);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st) {
   const int nb = vec_blocks(n);
 #define CA(TI_, TO_) k_cast<TI_, TO_><<<nb, kVecThreads, 0, st>>>(n, (const TI_*)x, (TO_*)y, c)

@@ -62,6 +62,8 @@ cudaError_t launch_dcgs_fused(const ProbDev& P, long long n, void* V, int j, boo
 cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, const void* w, GmresCtl* ctl,
                         RedWs red, unsigned int* err, int nsm, cudaStream_t st);
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);
+// Reset the line-search control of one Newton step (LsCtl): merit fnorm, trial alpha = 1.
+cudaError_t launch_ls_begin(LsCtl* c, double fnorm, double c1, double min_alpha, int accept_first, cudaStream_t st);
 cudaError_t launch_vdots(int t, long long n, int nd, const void* const* a, const void* const* b, double* sums,
                          RedWs red, const int* active, cudaStream_t st);
 // CG: phase 0 init (r = p = -F, d = 0), 1 p = r + beta p (not in the first

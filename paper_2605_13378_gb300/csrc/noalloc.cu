@@ -40,7 +40,9 @@ static_assert(kNaFxOffset + JFNK_NOALLOC_MAX_FX_BYTES == JFNK_NOALLOC_SCRATCH_BY
 static __device__ __align__(256) unsigned char g_noalloc_scratch[JFNK_NOALLOC_SCRATCH_BYTES];
 
 // Device address of g_noalloc_scratch per device, looked up once per device
-// with that device current (the host-side symbol is only a stand-in).
+// with that device current (the host-side symbol is only a stand-in) and kept
+// for the life of the process; a device reset unloads the array, after which
+// the kept address is stale (the header tells callers not to reset).
 constexpr int kNaMaxDevices = 64;
 static void* g_scratch_addr[kNaMaxDevices];
 static std::mutex g_scratch_mu;
@@ -127,6 +129,7 @@ extern "C" jfnk_status jfnk_jvp_fd_noalloc(const jfnk_problem* prob, int prec, c
   if (prec != JFNK_FP64 && prec != JFNK_FP32) return JFNK_E_INVALID;
   ProbDev P;
   if (!na_problem(prob, &P)) return JFNK_E_INVALID;
+  if (P.cfl > 0.0) return JFNK_E_INVALID;   // an adaptive step exists only inside jfnk_solve
   if (P.pde == JFNK_MAXWELL_TE2D && prec != JFNK_FP64) return JFNK_E_INVALID;   // eps_r, source are FP64
   const int t = prec == JFNK_FP64 ? VT_F64 : VT_F32;
   const size_t es = prec == JFNK_FP64 ? 8 : 4;

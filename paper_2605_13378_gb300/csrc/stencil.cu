@@ -44,10 +44,11 @@ static cudaError_t stencil_pde(int mode, const ProbDev& P, int t, int tv, const 
 }
 
 cudaError_t launch_residual(const ProbDev& P, int t, const void* x, const void* d, double alpha, const void* b,
-                            void* F, void* xout, float* x32, RedWs red, double* sums, cudaStream_t st) {
+                            void* F, void* xout, float* x32, RedWs red, double* sums, cudaStream_t st, LsCtl* ls) {
+  if (ls && !sums) return cudaErrorInvalidValue;   // the decision needs the reduced norm
   StencilArgs a;
   memset(&a, 0, sizeof(a));
-  a.x = x; a.v = d; a.alpha = alpha; a.b = b; a.F = F; a.xout = xout; a.x32 = x32; a.sums = sums;
+  a.x = x; a.v = d; a.alpha = alpha; a.b = b; a.F = F; a.xout = xout; a.x32 = x32; a.sums = sums; a.ls = ls;
   return stencil_pde(SM_RESID, P, t, t, a, red, st);
 }
 
@@ -67,6 +68,7 @@ cudaError_t launch_jvp(const ProbDev& P, const JvpArgs& in, RedWs red, cudaStrea
   a.post = in.post; a.post_arg = in.post_arg;
   a.eps_fixed = in.eps_fixed; a.eps_rule = in.eps_rule; a.xn2 = in.xn2; a.vn2 = in.vn2; a.eps_out = in.eps_out;
   a.active = in.active;
+  a.err = in.err;
   if (in.lin == 0) return stencil_pde(SM_AD, P, in.t, in.tv, a, red, st);
   return stencil_pde(SM_FD, P, in.t, in.tv, a, red, st);
 }

@@ -22,6 +22,7 @@
 
 #include "kernels.h"
 #include "ctl.cuh"
+#include "stream.cuh"
 
 namespace jfnk {
 
@@ -51,6 +52,8 @@ struct StencilArgs {
   const double* vn2;
   float* eps_out;
   const int* active;
+  LsCtl* ls;                // RESID: a line-search trial, alpha from ls->alpha (see LsCtl)
+  unsigned int* err;        // AD, FD: device error word of the staged form's bounded waits (null: march form)
 };
 
 template <class T> struct AccOf { typedef float type; };
@@ -159,7 +162,8 @@ __device__ __forceinline__ T fd_step(const StencilArgs& a, T s) {
         if (a.eps_rule == 1) {
           eps = sq * (xn > 1.0 ? xn : 1.0);
         } else {
-          const double vn = a.vn2 ? sqrt(*a.vn2) * (double)s : 1.0;
+          double vn = a.vn2 ? sqrt(*a.vn2) * (double)s : 1.0;
+          if (vn == 0.0) vn = 1.0;   // zero direction: keep the step finite (the quotient is then ~0)
           eps = sq * (1.0 + xn) / vn;
         }
       }
@@ -181,6 +185,9 @@ __device__ __forceinline__ void finish_reduction(const StencilArgs& a, Acc* acc,
   double* sums = a.sums;
   const bool last = grid_reduce<Acc, 3>(v3, nd, red, nblocks, blockLinear, sm,
                                         [&](int t, Acc sv) { sums[t] = (double)sv; });
+  if constexpr (MODE == SM_RESID) {
+    if (last && threadIdx.x == 0 && threadIdx.y == 0 && a.ls) ls_decide(a.ls, sums[0]);
+  }
   if constexpr (MODE == SM_AD || MODE == SM_FD) {
     if (last && threadIdx.x == 0 && threadIdx.y == 0 && a.post == POST_GMRES_RESTART)
       gmres_cycle_start((GmresCtl*)a.post_arg, sums[0]);
@@ -216,9 +223,10 @@ __global__ void __launch_bounds__(256) k_gather(ProbDev P, int R, StencilArgs a,
   typedef typename CB::V V;
   constexpr int NF = PDE::NF;
   if (a.active && *a.active == 0) return;
+  if (MODE == SM_RESID && a.ls && a.ls->done) return;
   const T s = (MODE == SM_AD || MODE == SM_FD) ? (a.vscale ? T(*a.vscale) : T(1)) : T(1);
   const T eps = fd_step<T, MODE>(a, s);
-  const CB cb = make_comb<MODE, T>(a.alpha, s, eps);
+  const CB cb = make_comb<MODE, T>((MODE == SM_RESID && a.ls) ? a.ls->alpha : a.alpha, s, eps);
   const T* __restrict__ x = (const T*)a.x;
   const TV* __restrict__ v = (const TV*)a.v;
   Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
@@ -441,9 +449,10 @@ __global__ void __launch_bounds__(256) k_march(ProbDev P, int nstrips, int R, St
   typedef Comb<MODE, T> CB;
   constexpr int NF = PDE::NF;
   if (a.active && *a.active == 0) return;
+  if (MODE == SM_RESID && a.ls && a.ls->done) return;
   const T s = (MODE == SM_AD || MODE == SM_FD) ? (a.vscale ? T(*a.vscale) : T(1)) : T(1);
   const T eps = fd_step<T, MODE>(a, s);
-  const CB cb = make_comb<MODE, T>(a.alpha, s, eps);
+  const CB cb = make_comb<MODE, T>((MODE == SM_RESID && a.ls) ? a.ls->alpha : a.alpha, s, eps);
   const bool usev = (MODE != SM_RHS) && a.v != nullptr;
   const int lane = threadIdx.x & 31;
   const long long gw = (long long)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
@@ -495,6 +504,12 @@ __global__ void __launch_bounds__(256) k_march(ProbDev P, int nstrips, int R, St
   }
   if constexpr (EPI == 0) finish_reduction<MODE, Acc>(a, acc, gridDim.x, blockIdx.x, red);
 }
+
+}  // namespace jfnk
+
+#include "stencil_stage.cuh"
+
+namespace jfnk {
 
 // --------------------------------------------------------------------------
 // geometry and launch
@@ -564,6 +579,16 @@ static cudaError_t stencil_launch(const ProbDev& P, const StencilArgs& a, RedWs 
       const bool plain = !a.F && !a.add && a.ndots == 0 && a.c_jv == 1.0 && aligned(a.out, 16) &&
                          (MODE != SM_FD || (aligned(a.Fx, 16) && aligned(a.b, 16)));
       if (plain) {
+        // large 2D grids: rows staged in shared memory by bulk copies (stencil_stage.cuh)
+        StagePlan sp;
+        if (a.err && P.nx >= kStageWarps * 32 * VEC && P.ny >= 64 && aligned(a.v, 16) &&
+            stage_plan<T, TV, PDE::NF>(P, num_sms(), &sp)) {
+          static SmemOptIn opt_in;
+          cudaError_t e = smem_opt_in(k_jvp_stage<PDE, T, TV, MODE>, opt_in, sp.smem);
+          if (e != cudaSuccess) return e;
+          k_jvp_stage<PDE, T, TV, MODE><<<sp.grid, kStageThreads, sp.smem, st>>>(P, a, sp);
+          return cudaGetLastError();
+        }
         k_march<PDE, T, TV, VEC, MODE, 1><<<g.nblocks, 256, 0, st>>>(P, g.nstrips, g.R, a, rs);
         return cudaGetLastError();
       }

@@ -12,6 +12,10 @@
 
 #include <stdint.h>
 
+#include <atomic>
+
+#include <cuda_runtime.h>
+
 #include "common.cuh"
 
 namespace jfnk {
@@ -65,6 +69,16 @@ __device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity
   }
 }
 
+// Wait for phase `parity` of `bar` until the global timer passes `deadline_ns`;
+// false on expiry. Draining several barriers against one deadline bounds the
+// whole drain, not each wait.
+__device__ __forceinline__ bool mbar_wait_until(uint64_t* bar, uint32_t parity, uint64_t deadline_ns) {
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (global_timer_ns() > deadline_ns) return false;
+  }
+}
+
 // Bulk copy global -> shared, completing `bytes` on `bar` (16-byte aligned
 // addresses, bytes a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -78,6 +92,26 @@ __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t by
 constexpr uint64_t kWaitLimitNs = 1000000000ull;   // one second
 constexpr int kStreamThreads = 256;
 constexpr int kStreamSmem = 200 * 1024;            // ring budget per CTA
+
+// Opt-in of a kernel to more than 48 KB of dynamic shared memory. The
+// attribute belongs to the kernel on one device, so the flag that records it
+// is kept per device ordinal (a process may launch on several GPUs).
+constexpr int kOptInDevices = 64;
+struct SmemOptIn {
+  std::atomic<bool> done[kOptInDevices];
+};
+template <class K>
+inline cudaError_t smem_opt_in(K* kernel, SmemOptIn& f, int bytes) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < kOptInDevices;
+  if (cached && f.done[dev].load(std::memory_order_acquire)) return cudaSuccess;
+  e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, bytes);
+  if (e != cudaSuccess) return e;
+  if (cached) f.done[dev].store(true, std::memory_order_release);
+  return cudaSuccess;
+}
 
 // Error codes written to the device error word.
 enum StreamErr { STREAM_OK = 0, STREAM_TIMEOUT = 1 };

@@ -163,8 +163,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
       __syncwarp();
     }
     if (s_abort && lane == 0) {
+      const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (it - kStages > 0 ? it - kStages : 0); q < it; ++q)
-        mbar_wait_bounded(&full[q % kStages], (uint32_t)((q / kStages) & 1), kWaitLimitNs);
+        mbar_wait_until(&full[q % kStages], (uint32_t)((q / kStages) & 1), deadline);
     }
   } else {
     // ---------------- consumers ----------------
@@ -356,8 +357,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
       __syncwarp();
     }
     if (s_abort && lane == 0) {
+      const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (it - kResStages > 0 ? it - kResStages : 0); q < it; ++q)
-        mbar_wait_bounded(&full[q % kResStages], (uint32_t)((q / kResStages) & 1), kWaitLimitNs);
+        mbar_wait_until(&full[q % kResStages], (uint32_t)((q / kResStages) & 1), deadline);
     }
   } else {
     const int ctid = tid - 32;
@@ -433,13 +435,9 @@ static cudaError_t resident2_launch(long long n, const void* V, int k, void* w, 
   *used = scb > 0;
   if (!*used) return cudaSuccess;
   const size_t smem = (size_t)kResStages * stage + (size_t)kResStages * 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_basis_resident2<TB, TJ, KMAX>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         kResStages * kResBudget + 64);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static SmemOptIn opt_in;
+  cudaError_t e = smem_opt_in(k_basis_resident2<TB, TJ, KMAX>, opt_in, kResStages * kResBudget + 64);
+  if (e != cudaSuccess) return e;
   k_basis_resident2<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
       n, (const TB*)V, n, k, (TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage, err);
   return cudaGetLastError();
@@ -455,13 +453,9 @@ static cudaError_t stream_launch(long long n, const void* V, int k, int kmax, vo
   const int wbytes = CE * (int)sizeof(TJ);
   if (wbytes > stage) stage = wbytes;
   const size_t smem = (size_t)kStages * stage + (size_t)kStages * 16;
-  static bool attr_set = false;
-  if (!attr_set) {
-    cudaError_t e = cudaFuncSetAttribute(k_basis_stream<TB, TJ, TD, KMAX, MODE>,
-                                         cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-    if (e != cudaSuccess) return e;
-    attr_set = true;
-  }
+  static SmemOptIn opt_in;
+  cudaError_t e = smem_opt_in(k_basis_stream<TB, TJ, TD, KMAX, MODE>, opt_in, (int)smem);
+  if (e != cudaSuccess) return e;
   k_basis_stream<TB, TJ, TD, KMAX, MODE><<<nsm, kStreamThreads + 32, smem, st>>>(
       n, (const TB*)V, n, k, (TJ*)w, (TD*)d, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, stage,
       err);

@@ -28,7 +28,7 @@ JFNK_GMRES, JFNK_BICGSTAB, JFNK_CG = 0, 1, 2
 JFNK_BURGERS1D, JFNK_ALLEN_CAHN2D, JFNK_SU_OLSON2D, JFNK_MAXWELL_TE2D, JFNK_BURGERS2D = 0, 1, 2, 3, 4
 JFNK_FP64, JFNK_FP32, JFNK_MIXED_FP32, JFNK_MIXED_BF16 = 0, 1, 2, 3
 JFNK_EPS_SCALED, JFNK_EPS_PAPER = 0, 1
-JFNK_CGS2, JFNK_DCGS2 = 0, 1
+JFNK_CGS2, JFNK_DCGS2, JFNK_DCGS2_FUSED = 0, 1, 2
 JFNK_MAX_RESTART = 64
 
 EXPORTED = ["jfnk_default_opts", "jfnk_create", "jfnk_set_problem", "jfnk_jvp", "jfnk_residual", "jfnk_solve",
@@ -53,10 +53,11 @@ class jfnk_report(C.Structure):
     _fields_ = [("status", C.c_int), ("steps_done", C.c_int), ("steps_failed", C.c_int), ("newton_its", C.c_int),
                 ("krylov_its", C.c_int), ("jvp_calls", C.c_int), ("ls_backtracks", C.c_int),
                 ("ls_failures", C.c_int), ("krylov_failures", C.c_int), ("res0", C.c_double),
-                ("res_final", C.c_double), ("ms", C.c_double), ("dt_last", C.c_double)]
+                ("res_final", C.c_double), ("ms", C.c_double), ("dt_last", C.c_double),
+                ("ls_alpha", C.c_double * 16)]
 
     def as_dict(self) -> dict:
-        return {k: getattr(self, k) for k, _ in self._fields_}
+        return {k: (list(getattr(self, k)) if k == "ls_alpha" else getattr(self, k)) for k, _ in self._fields_}
 
 
 _P = C.c_void_p

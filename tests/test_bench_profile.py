@@ -57,3 +57,8 @@ def test_src_hash_follows_code_not_comments(tmp_path, monkeypatch):
     k.write_text("__global__ void k(float* x) { x[0] = 1.0f; }\n")
     (csrc / "extra.cuh").write_text("")
     assert bench._src_hash() != h0          # a new file counts, even an empty one
+
+
+def test_strip_comments_keeps_literal_spacing():
+    assert bench._strip_comments('f("a  b",   1);') == 'f("a  b", 1);'
+    assert bench._strip_comments('f("a b", 1);') != bench._strip_comments('f("a  b", 1);')

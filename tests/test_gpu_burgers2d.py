@@ -167,3 +167,26 @@ def test_undefined_rule_and_nonfinite_state(J, ctx):
     s, _, rep = _run(J, ctx, _lp(J, n, n, 0.05, 1.0), _opts(J, J.JFNK_FP64), bad, 2)
     assert s == J.JFNK_E_NONFINITE
     assert rep.steps_failed == 1 and rep.steps_done == 0 and np.isnan(rep.dt_last)
+
+
+def test_jvp_and_residual_refuse_an_adaptive_step(J, ctx):
+    """With the CFL rule (C > 0) the time step exists only inside jfnk_solve: the standalone JVP and
+    residual entry points refuse such a problem instead of using dt = 0; with C = 0 and a step they run."""
+    n = 16
+    x = torch.tensor(si.burgers2d_ic(n, n, "tgv"), device="cuda")
+    out = torch.zeros_like(x)
+    J.check(ctx, J.jfnk_set_problem(ctx, _lp(J, n, n, 0.05, 1.0)), "set_problem")
+    for lin in (J.JFNK_AD, J.JFNK_FD):
+        assert J.jfnk_jvp(ctx, lin, J.JFNK_FP64, x, x, None, None, out, 0.0) == J.JFNK_E_INVALID
+        assert "adaptive" in J.jfnk_last_error(ctx)
+    assert J.jfnk_residual(ctx, J.JFNK_FP64, x, None, out) == J.JFNK_E_INVALID
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(out).item() == 0
+    J.check(ctx, J.jfnk_set_problem(ctx, J.make_problem("burgers2d", n, n, 1e-3, 0.5, (0.05, 0.0, 0.0))), "set")
+    assert J.jfnk_jvp(ctx, J.JFNK_AD, J.JFNK_FP64, x, x, None, None, out, 0.0) == J.JFNK_OK
+    torch.cuda.synchronize()
+    p = opdes.Burgers2D(nx=n, ny=n, nu=0.05, dt=1e-3)
+    from oracle import jvp as ojvp
+    xh = x.cpu().numpy()
+    _, Jv = ojvp.jvp_complex_step(lambda z: p.residual(z, np.zeros_like(z)), xh, xh)
+    assert np.abs(out.cpu().numpy() - Jv).max() <= 1e-12 * np.abs(Jv).max()

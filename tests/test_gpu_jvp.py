@@ -226,3 +226,73 @@ def test_invalid_problems_are_rejected(J, ctx):
     assert J.jfnk_set_problem(ctx, J.make_problem("burgers2d", 16, 16, 0.0, 0.5, (0.1, 0.0, 0.0))) == J.JFNK_E_INVALID
     # with a Courant number the step is adaptive and dt is not needed
     assert J.jfnk_set_problem(ctx, J.make_problem("burgers2d", 16, 16, 0.0, 0.5, (0.1, 0.0, 1.0))) == J.JFNK_OK
+
+
+# The plain Krylov product (no F output, no addend) on 2D grids with rows of at least 1024 FP32 or 512
+# FP64 cells and at least 64 rows runs the staged form: rows of x and v copied into shared memory by bulk
+# copies, one CTA per (strip, band) unit. These cases give ragged last strips (1028 = 1024 + 4 columns;
+# 3 strips of 512 + 4 in FP64), ragged last bands, both wall policies (wrap: Allen-Cahn, 2D Burgers;
+# clamp: radiation, Maxwell, Dirichlet walls) and, at 3072 x 408 (3 strips x 102 bands of 4 rows on 304
+# CTAs), CTAs that take a second unit.
+STAGED = [("allen_cahn", 1028, 70), ("su_olson", 1024, 66), ("maxwell", 1028, 64), ("burgers2d", 1024, 65),
+          ("rd_dirichlet", 1028, 67), ("allen_cahn", 3072, 408)]
+
+
+@pytest.mark.parametrize("name,nx,ny", STAGED)
+def test_staged_ad_jvp_fp64_matches_complex_step(J, ctx, name, nx, ny):
+    p, lp, x, v, b, _ = _case(name, nx, ny)
+    J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+    xt, vt, bt = _dev(x), _dev(v), _dev(b)
+    Jv = torch.full_like(xt, float("nan"))
+    J.check(ctx, J.jfnk_jvp(ctx, J.JFNK_AD, J.JFNK_FP64, xt, vt, bt, None, Jv, 0.0), "jvp")
+    torch.cuda.synchronize()
+    _, Jv_ref = ojvp.jvp_complex_step(lambda z: p.residual(z, b), x, v)
+    assert np.abs(Jv.cpu().numpy() - Jv_ref).max() <= 1e-12 * np.abs(Jv_ref).max()
+
+
+@pytest.mark.parametrize("name,nx,ny", STAGED)
+def test_staged_ad_jvp_fp32_matches_oracle_on_rounded_inputs(J, ctx, name, nx, ny):
+    p, lp, x, v, b, _ = _case(name, nx, ny)
+    x = x.astype(np.float32).astype(np.float64)
+    v = v.astype(np.float32).astype(np.float64)
+    b = None if b is None else b.astype(np.float32).astype(np.float64)
+    if name == "maxwell":
+        p.eps_r = p.eps_r.astype(np.float32).astype(np.float64)
+    J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+    xt, vt, bt = _dev(x, torch.float32), _dev(v, torch.float32), _dev(b, torch.float32)
+    Jv = torch.full_like(xt, float("nan"))
+    J.check(ctx, J.jfnk_jvp(ctx, J.JFNK_AD, J.JFNK_FP32, xt, vt, bt, None, Jv, 0.0), "jvp")
+    torch.cuda.synchronize()
+    _, Jv_ref = ojvp.jvp_complex_step(lambda z: p.residual(z, b), x, v)
+    assert np.abs(Jv.cpu().numpy() - Jv_ref).max() <= 5e-5 * np.abs(Jv_ref).max()
+
+
+@pytest.mark.parametrize("name,nx,ny", STAGED[:3])
+def test_staged_fd_jvp_fp64_matches_oracle_quotient(J, ctx, name, nx, ny):
+    p, lp, x, v, b, _ = _case(name, nx, ny)
+    J.check(ctx, J.jfnk_set_problem(ctx, lp), "set_problem")
+    F = lambda z: p.residual(z, b)
+    ref = ojvp.jvp_fd(F, x, v, ojvp.fd_eps_scaled(x, v))
+    scale = np.abs(ojvp.jvp_complex_step(F, x, v)[1]).max()
+    xt, vt, bt = _dev(x), _dev(v), _dev(b)
+    out = torch.full_like(xt, float("nan"))
+    J.check(ctx, J.jfnk_jvp(ctx, J.JFNK_FD, J.JFNK_FP64, xt, vt, bt, None, out, 0.0), "jvp")
+    torch.cuda.synchronize()
+    assert np.abs(out.cpu().numpy() - ref).max() <= 1e-6 * scale
+
+
+def test_staged_ad_jvp_fp32_full_size_allen_cahn_2048(J, ctx):
+    """The product the benchmark's Krylov loop applies: FP32 AD, plain output, 2048^2 grid."""
+    n = 2048
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    x = si.allen_cahn_ic(n, n, 0).astype(np.float32).astype(np.float64)
+    v = np.random.default_rng(4).standard_normal(n * n).astype(np.float32).astype(np.float64)
+    b = p.rhs(x).astype(np.float32).astype(np.float64)
+    J.check(ctx, J.jfnk_set_problem(ctx, J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))), "set")
+    xt, vt, bt = _dev(x, torch.float32), _dev(v, torch.float32), _dev(b, torch.float32)
+    Jv = torch.full_like(xt, float("nan"))
+    for _ in range(2):   # the second launch reuses the ring's barriers from a fresh launch
+        J.check(ctx, J.jfnk_jvp(ctx, J.JFNK_AD, J.JFNK_FP32, xt, vt, bt, None, Jv, 0.0), "jvp")
+    torch.cuda.synchronize()
+    _, Jv_ref = ojvp.jvp_complex_step(lambda z: p.residual(z, b), x, v)
+    assert np.abs(Jv.cpu().numpy() - Jv_ref).max() <= 5e-5 * np.abs(Jv_ref).max()

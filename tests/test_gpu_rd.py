@@ -9,7 +9,6 @@ FP64 (1e-5 mixed), equal Newton counts, Krylov counts within 2 per Newton
 step; also the batch engine, delayed CGS2 and its opt-in fused pass, and the
 paper's 512^2 GPU grid.
 """
-import os
 
 import numpy as np
 import pytest
@@ -98,13 +97,8 @@ def test_mixed_delayed_cgs2(J, ctx, fused):
     n, D = 64, 0.001
     p, lp = _problem(J, n, D)
     u0 = si.rd_ic(n, n, "multigauss")
-    if fused:
-        os.environ["JFNK_FUSED"] = "1"
-    try:
-        s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_MIXED_FP32, "ad", "gmres", 40, 1e-9, 1e-5, max_newton=30,
-                                           ortho=J.JFNK_DCGS2), u0, 2)
-    finally:
-        os.environ.pop("JFNK_FUSED", None)
+    s, x, rep = _run(J, ctx, lp, _opts(J, J.JFNK_MIXED_FP32, "ad", "gmres", 40, 1e-9, 1e-5, max_newton=30,
+                                       ortho=J.JFNK_DCGS2_FUSED if fused else J.JFNK_DCGS2), u0, 2)
     assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
     x_ref, reps = onw.time_steps(p, u0, 2, _oopts("ad", "gmres", 40, 1e-12, 1e-12))
     assert np.abs(x - x_ref).max() / np.abs(x_ref).max() <= 1e-5

@@ -228,7 +228,9 @@ def test_hbm_budget_is_enforced(J):
 
 
 def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
-    """The benchmark grid (2048^2) in FP64 against the oracle's stored solve (tests/golden/)."""
+    """The benchmark grid (2048^2) in FP64 at tol_Newton = tol_Krylov = 1e-8 against the oracle's stored solve
+    at the same tolerances (tests/golden/): Newton and Krylov counts and the full-size residual. The solution
+    itself is compared with a reference solved well below the tolerance in test_gpu_reference_2048.py."""
     import json
     import os
     g = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "allen_cahn_2048_step1.json")))
@@ -242,9 +244,6 @@ def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
     assert abs(rep.krylov_its - g["krylov_its"]) <= 2 * g["newton_its"], (rep.krylov_its, g["krylov_its"])
     # residual recomputed by the oracle at full size
     assert np.linalg.norm(p.residual(x, p.rhs(u0))) <= 1e-8 * g["res0"]
-    xs = np.array([x[i] for i in g["sample_idx"]])
-    assert np.abs(xs - np.array(g["x_samples"])).max() <= 1e-9 * g["x_absmax"]
-    assert abs(x.sum() - g["x_sum"]) <= 1e-9 * g["x_absmax"] * x.size
 
 
 @pytest.mark.parametrize("lin", ["ad", "fd"])

@@ -48,6 +48,12 @@ def _case(J, name, dtype):
         x = si.burgers_ic(1024, 0)
         b = opdes.Burgers1D(N=1024).rhs(x)
         keep = ()
+    elif name == "burgers2d":
+        nx, ny = 48, 40                       # fixed step (Courant number 0): the step is the caller's dt
+        lp = J.make_problem("burgers2d", nx, ny, 2e-3, 0.5, (0.05, 0.0, 0.0))
+        x = si.burgers2d_ic(nx, ny, "tgv") + 0.1 * rng.standard_normal(2 * nx * ny)
+        b = opdes.Burgers2D(nx=nx, ny=ny, nu=0.05, dt=2e-3).rhs(x)
+        keep = ()
     elif name == "su_olson":
         nx = ny = 40
         lp = J.make_problem("su_olson", nx, ny, 1e-2, 0.5, (1.0, 1.0, 1.0, 1e-6, 1.0))
@@ -81,7 +87,7 @@ def _reference(J, lp, prec, x, v, b, fd_eps):
 
 
 @pytest.mark.parametrize("name,prec", [("allen_cahn", "fp64"), ("burgers", "fp64"), ("su_olson", "fp64"),
-                                       ("maxwell", "fp64"), ("allen_cahn", "fp32")])
+                                       ("maxwell", "fp64"), ("burgers2d", "fp64"), ("allen_cahn", "fp32")])
 def test_noalloc_fd_jvp_matches_context_entry_point(J, name, prec):
     dtype = torch.float64 if prec == "fp64" else torch.float32
     code = J.JFNK_FP64 if prec == "fp64" else J.JFNK_FP32
@@ -123,3 +129,33 @@ def test_noalloc_refuses_what_does_not_fit(J):
     lm = J.make_problem("maxwell", 16, 16, 0.0, 1.0, (3.0, 0.1))
     x32 = torch.zeros(2 * 256, dtype=torch.float32, device="cuda")
     assert J.jfnk_jvp_fd_noalloc(lm, J.JFNK_FP32, x32, x32, None, None, x32.clone(), 0.0) == J.JFNK_E_INVALID
+
+
+@pytest.mark.parametrize("prec", ["fp64", "fp32"])
+def test_noalloc_zero_direction_gives_zero(J, prec):
+    """J 0 = 0: with v = 0 the step rule takes ||v|| = 1, so the step stays finite and the quotient is
+    (F(x) - F(x)) / eps, zero up to the rounding of F(x) between the two sweeps -- as in jfnk_jvp."""
+    dtype = torch.float64 if prec == "fp64" else torch.float32
+    code = J.JFNK_FP64 if prec == "fp64" else J.JFNK_FP32
+    tol = 1e-6 if prec == "fp64" else 1e-3
+    lp, x, _, b, _keep = _case(J, "allen_cahn", dtype)
+    v = torch.zeros_like(x)
+    F_ref, Jv_ref = _reference(J, lp, code, x, v, b, 0.0)
+    bound = tol * F_ref.abs().max().item()
+    assert torch.isfinite(Jv_ref).all() and Jv_ref.abs().max().item() <= bound
+    for _ in range(2):
+        Jv = torch.full_like(x, np.nan)
+        assert J.jfnk_jvp_fd_noalloc(lp, code, x, v, b, None, Jv, 0.0) == J.JFNK_OK
+        torch.cuda.synchronize()
+        assert torch.isfinite(Jv).all() and Jv.abs().max().item() <= bound
+
+
+def test_noalloc_refuses_an_adaptive_step(J):
+    """A 2D Burgers problem whose step comes from the CFL rule has no step outside jfnk_solve."""
+    nx, ny = 32, 32
+    lp = J.make_problem("burgers2d", nx, ny, 0.0, 0.5, (0.05, 0.0, 1.0))
+    x = torch.tensor(si.burgers2d_ic(nx, ny, "tgv"), device="cuda")
+    Jv = torch.zeros_like(x)
+    assert J.jfnk_jvp_fd_noalloc(lp, J.JFNK_FP64, x, x, None, None, Jv, 0.0) == J.JFNK_E_INVALID
+    torch.cuda.synchronize()
+    assert torch.count_nonzero(Jv).item() == 0
