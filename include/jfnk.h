@@ -73,9 +73,25 @@ typedef enum {
                              p[4] = 1 flux limiter on / 0 off                        */
   JFNK_MAXWELL_TE2D = 3,  /* p[0] = k, p[1] = chi3; aux[0] = eps_r (nx*ny),
                              aux[1] = source (Re plane, Im plane; 2*nx*ny)           */
-  JFNK_BURGERS2D = 4      /* p[0] = nu >= 0, p[1] = side L of the periodic square
+  JFNK_BURGERS2D = 4,     /* p[0] = nu >= 0, p[1] = side L of the periodic square
                              (0: 2 pi), p[2] = Courant number C (0: fixed dt)       */
+  JFNK_MAXWELL_VEC2D = 5  /* p[0] = w > 0, p[1] = chi >= 0, p[2] = loss L >= 0 (the
+                             paper's 0.05); aux[0] unused (NULL), aux[1] = current J
+                             (Re Jx, Im Jx, Re Jy, Im Jy planes; 4*nx*ny)            */
 } jfnk_pde;
+/* JFNK_MAXWELL_VEC2D is the paper's vector TE Maxwell problem in a Kerr
+ * medium (App. A, Time-Harmonic Maxwell's Equations in Kerr Media): the
+ * boundary-value problem curl curl E - w^2 eps(E) E = i w J with
+ * eps(E) = (1 - L i)(1 + chi |E|), |E| = sqrt(|Ex|^2 + |Ey|^2), E = (Ex, Ey)
+ * on the nodes x_i = i/(nx - 1), y_j = j/(ny - 1) of the unit square, whose
+ * walls are perfect electric conductors: the rows of the tangential component
+ * on a wall are F = E_t, and a neighbour beyond a wall is the image across it
+ * (tangential component odd, normal even). State planes [Re Ex, Im Ex, Re Ey,
+ * Im Ey]; central differences of the curl-curl operator with the mixed
+ * derivative on the four corner neighbours; |E| = 0 takes a zero derivative.
+ * jfnk_solve starts from the Born guess (the chi = 0 problem solved from
+ * zero) when opts.born_start is set; the paper's continuation over the
+ * frequency w is a sequence of such solves (jfnk_set_problem per w). */
 /* JFNK_BURGERS2D is the paper's 2D viscous Burgers problem (App. A, Burgers'
  * Equation): U = (u, v) on nodes x_i = i L/nx, y_j = j L/ny of the periodic
  * square, second-order central differences for the advection u D_x U +
@@ -93,6 +109,16 @@ typedef enum {
   JFNK_MIXED_BF16 = 3   /* as MIXED_FP32 with the GMRES basis stored in BF16                  */
 } jfnk_precision;
 typedef enum { JFNK_EPS_SCALED = 0, JFNK_EPS_PAPER = 1 } jfnk_fd_rule;
+/* Right preconditioner of GMRES for the vector Maxwell problem: the paper's
+ * block-diagonal complex-shifted-Laplacian (App. A, Preconditioning), per
+ * node M_xx = 2/hy^2 - w^2 eps_p, M_yy = 2/hx^2 - w^2 eps_p with
+ * eps_p = eps(E)(1 - beta i) at the current Newton iterate (beta =
+ * opts.precond_damping, the paper's 0.5), 1 on the rows of the tangential
+ * components on the walls. GMRES solves J M^-1 y = -F (every Jacobian-vector
+ * product applies M^-1 to its direction first, AD or FD) and the Newton step
+ * is d = M^-1 y. Only with krylov = JFNK_GMRES and the vector Maxwell
+ * problem (JFNK_E_INVALID otherwise). */
+typedef enum { JFNK_PRECOND_NONE = 0, JFNK_PRECOND_CSLP = 1 } jfnk_precond;
 /* Arnoldi orthogonalisation of GMRES (Sec. 3): classical Gram-Schmidt applied
  * twice, or the same two passes with the second one delayed by one Arnoldi
  * step (delayed CGS2), which fuses them into one dots pass and one update
@@ -117,11 +143,12 @@ typedef enum { JFNK_CGS2 = 0, JFNK_DCGS2 = 1, JFNK_DCGS2_FUSED = 2 } jfnk_ortho;
  * Maxwell problem is a boundary-value problem, F = G (dt, theta unused). */
 typedef struct {
   int pde;            /* jfnk_pde */
-  int nx, ny;         /* cells; ny = 1 for Burgers */
+  int nx, ny;         /* cells (nodes for JFNK_MAXWELL_VEC2D); ny = 1 for Burgers */
   double dt, theta;
   double p[8];        /* PDE parameters, see jfnk_pde */
-  const double* aux[2];  /* Maxwell eps_r and source, FP64, host or device;
-                            copied by jfnk_set_problem; NULL: eps_r = 1, no source */
+  const double* aux[2];  /* Maxwell eps_r and source (the vector form: aux[1] = J), FP64,
+                            host or device; copied by jfnk_set_problem; NULL: eps_r = 1,
+                            no source */
 } jfnk_problem;
 
 typedef struct {
@@ -139,6 +166,8 @@ typedef struct {
   double ls_min_alpha;/* smallest trial step; accepted when no trial passes */
   int born_start;     /* Maxwell: solve the chi3 = 0 problem from zero first */
   int ortho;          /* jfnk_ortho (GMRES) */
+  int precond;        /* jfnk_precond (GMRES, vector Maxwell) */
+  double precond_damping;  /* beta of eps_p = eps(E)(1 - beta i); the paper's 0.5 */
 } jfnk_opts;
 
 typedef struct {
@@ -158,7 +187,7 @@ typedef struct {
 /* Defaults of the paper for a precision (Sec. 3.3): tol_Newton 1e-6 / 1e-4,
  * tol_Krylov 1e-8 / 1e-6 (FP64 / FP32), 15 Newton iterations, 100 Krylov
  * cycles, GMRES(30) with CGS2, AD, scaled FD rule, c1 = 1e-4,
- * alpha_min = 2^-10. */
+ * alpha_min = 2^-10, no preconditioner (damping 0.5 when one is chosen). */
 void jfnk_default_opts(jfnk_opts* opts, int prec);
 
 /* Create a context on CUDA device `device`. hbm_budget caps the workspace

@@ -20,7 +20,7 @@ INCLUDE = os.path.join(ROOT, "include")
 OBJDIR = os.path.join(PKG, "_build")
 LIB = os.path.join(PKG, "libjfnk.so")
 SOURCES = ["stencil.cu", "stencil_burgers.cu", "stencil_allen_cahn.cu", "stencil_su_olson.cu", "stencil_maxwell.cu",
-           "stencil_burgers2d.cu",
+           "stencil_burgers2d.cu", "stencil_maxwell_vec.cu",
            "krylov.cu", "stream_f64.cu", "stream_f32.cu", "stream_bf16.cu", "jfnk.cu", "serve.cu",
            "noalloc.cu", "problem.cu", "batch.cu", "batch_burgers.cu", "batch_allen_cahn.cu", "batch_su_olson.cu",
            "batch_maxwell.cu", "batch_burgers2d.cu", "dcgs_fused.cu", "dcgs_fused_allen_cahn.cu",

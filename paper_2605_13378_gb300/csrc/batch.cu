@@ -130,6 +130,10 @@ bool BatchEngine::supports(const jfnk_problem* pr, const jfnk_opts* o, std::stri
   if (!(o->ls_min_alpha > 0.0 && o->ls_min_alpha <= 1.0)) { if (why) *why = "bad ls_min_alpha"; return false; }
   if (o->fd_rule != JFNK_EPS_SCALED && o->fd_rule != JFNK_EPS_PAPER) { if (why) *why = "bad fd_rule"; return false; }
   if (o->ortho != JFNK_CGS2) { if (why) *why = "batched solves use CGS2 Arnoldi"; return false; }
+  if (pr->pde == JFNK_MAXWELL_VEC2D || o->precond != JFNK_PRECOND_NONE) {
+    if (why) *why = "the vector Maxwell problem and its preconditioner run through jfnk_solve";
+    return false;
+  }
   return true;
 }
 

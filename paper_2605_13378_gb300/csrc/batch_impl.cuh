@@ -64,7 +64,7 @@ __device__ __forceinline__ void bat_cells(const ProbDev& P, long long c0, long l
       }
     }
     CellAux<T> aux;
-    aux.eps = T(1); aux.fr = T(0); aux.fi = T(0);
+    aux.eps = T(1); aux.fr = T(0); aux.fi = T(0); aux.gr = T(0); aux.gi = T(0);
     if constexpr (PDE::AUX) {
       const T* ep = eps_of<T>(P);
       const T* sp = src_of<T>(P);

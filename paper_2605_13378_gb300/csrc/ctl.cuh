@@ -20,7 +20,8 @@ struct GmresCtl {
   int converged, breakdown, nonfinite;
   int its;                         // Arnoldi steps over all cycles
   int pad_;
-  volatile int* host_active;       // mapped host word mirroring `active` (may be null)
+  volatile int* host_active;       // mapped host words (may be null): [0] mirrors `active`, [1] the
+                                   // delayed-CGS2 steps completed in this cycle (dcgs_after_update)
   // arrays
   double H[(kMaxM + 1) * kMaxM];   // Hessenberg, column-major H[j * (kMaxM + 1) + i], rotated in place
   double h1[kMaxM + 1];            // first Gram-Schmidt pass of column j
@@ -425,6 +426,10 @@ __device__ __forceinline__ void dcgs_after_update(GmresCtl* c, int j, double n2)
     mirror_active(c->host_active, 0);
   } else {
     c->scale[j + 1] = n2 > 0.0 ? 1.0 / sqrt(n2) : 0.0;
+  }
+  if (c->host_active) {   // step j done: the host's lookahead bound, without a stream event
+    c->host_active[1] = j + 1;
+    __threadfence_system();
   }
 }
 

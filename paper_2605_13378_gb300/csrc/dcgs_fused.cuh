@@ -337,7 +337,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1) k_dcgs_fused(FusedArgs
             qn.s[f] = Dual<float>(xring[(xs * NF + f) * sw + p], uring[(us * NF + f) * sw + p]);
           }
           CellAux<float> aux;
-          aux.eps = 1.0f; aux.fr = 0.0f; aux.fi = 0.0f;
+          aux.eps = 1.0f; aux.fr = 0.0f; aux.fi = 0.0f; aux.gr = 0.0f; aux.gi = 0.0f;
           if constexpr (PDE::AUX) {
             const float* ep = P.eps32;
             if (ep) aux.eps = ep[(long long)r * nx + c];

@@ -9,8 +9,9 @@
 // Each reads basis slots 0..j and w once, against three passes of CGS2.
 // Resident form: one super-chunk of every vector involved fills one entry of
 // a shared-memory ring (bulk copies by producer warp 0, eight consumer warps);
-// the ring has as many entries as fit 200 KB, so that short passes keep more
-// than one entry in flight while the consumers read another. Requires
+// the ring has as many entries as fit the device's per-block limit (227 KB on
+// GB300, less the kernel's static shared memory), so that short passes keep
+// more than one entry in flight while the consumers read another. Requires
 // n % 8 == 0, like the other streaming passes.
 #pragma once
 
@@ -20,7 +21,6 @@
 
 namespace jfnk {
 
-constexpr int kDcgsRing = 200 * 1024;     // bytes of the ring
 constexpr int kDcgsBudget = 100 * 1024;   // largest entry: two entries always fit
 constexpr int kDcgsMaxStages = 32;
 
@@ -86,6 +86,8 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   constexpr int GT = kStreamThreads / 2;       // threads per group (split form)
   constexpr bool kJoint = sizeof(A) == 4 && KMAX <= 24;   // chunks of at least 256 slices: every thread busy
   constexpr int NW = kJoint ? NA : 1;          // w accumulators of the joint form
+  grid_dep_wait();      // the JVP that wrote w has completed (programmatic launch)
+  grid_dep_trigger();
   if (!ctl->active || (int)gridDim.x > cap) return;   // host sizing error: never write past the partials
   extern __shared__ __align__(128) unsigned char sring[];
   uint64_t* full = (uint64_t*)(sring + (size_t)nst * stage_bytes);
@@ -419,6 +421,8 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
                   RedSite<typename AccS<TJ>::type> red, int scb, int stage_bytes, int nst, unsigned int* err) {
   typedef typename AccS<TJ>::type A;
   constexpr int VW = 16 / (int)sizeof(TB);
+  grid_dep_wait();      // the dots pass that formed the coefficients has completed
+  grid_dep_trigger();
   if (!ctl->active) return;
   extern __shared__ __align__(128) unsigned char sring[];
   uint64_t* full = (uint64_t*)(sring + (size_t)nst * stage_bytes);
@@ -513,36 +517,46 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
 
 template <class TB, class TJ, int KMAX>
 static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                                 unsigned int* err, int nsm, cudaStream_t st) {
+                                 unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
   typedef typename AccS<TJ>::type A;
   int stage = 0;
   const int scb = dcgs_scb<TB, TJ>(j + 1, w != nullptr, &stage);
   if (scb == 0) return cudaErrorInvalidValue;
-  int nst = kDcgsRing / stage;                          // ring entries, at least two
-  if (nst > kDcgsMaxStages) nst = kDcgsMaxStages;
-  const size_t smem = (size_t)nst * stage + (size_t)nst * 16;
+  // as many ring entries (and their two barriers) as the per-block limit holds
+  static SmemLimit limit_of[2];
   static SmemOptIn opt_in[2];
-  cudaError_t e = pass == 1 ? smem_opt_in(k_dcgs_dots<TB, TJ, KMAX>, opt_in[0], kDcgsRing + kDcgsMaxStages * 16)
-                            : smem_opt_in(k_dcgs_update<TB, TJ, KMAX>, opt_in[1], kDcgsRing + kDcgsMaxStages * 16);
+  int limit = 0;
+  cudaError_t e = pass == 1 ? smem_block_limit(k_dcgs_dots<TB, TJ, KMAX>, limit_of[0], &limit)
+                            : smem_block_limit(k_dcgs_update<TB, TJ, KMAX>, limit_of[1], &limit);
+  if (e != cudaSuccess) return e;
+  int nst = limit / (stage + 16);
+  if (nst > kDcgsMaxStages) nst = kDcgsMaxStages;
+  if (nst < 2) return cudaErrorInvalidValue;               // two entries always fit on GB300 (kDcgsBudget)
+  const size_t smem = (size_t)nst * stage + (size_t)nst * 16;
+  e = pass == 1 ? smem_opt_in(k_dcgs_dots<TB, TJ, KMAX>, opt_in[0], limit)
+                : smem_opt_in(k_dcgs_update<TB, TJ, KMAX>, opt_in[1], limit);
   if (e != cudaSuccess) return e;
   if (pass == 1)
-    k_dcgs_dots<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
-        n, (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb, stage, nst, err);
+    e = launch_maybe_pdl(pdl, k_dcgs_dots<TB, TJ, KMAX>, dim3(nsm), dim3(kStreamThreads + 32), smem, st, n,
+                         (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb,
+                         stage, nst, err);
   else
-    k_dcgs_update<TB, TJ, KMAX><<<nsm, kStreamThreads + 32, smem, st>>>(
-        n, (TB*)V, j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage, nst, err);
+    e = launch_maybe_pdl(pdl, k_dcgs_update<TB, TJ, KMAX>, dim3(nsm), dim3(kStreamThreads + 32), smem, st, n, (TB*)V,
+                         j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage,
+                         nst, err);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
 // pass 1: dots of step j (w null: the last step of a cycle); pass 2: update of step j
 template <class TB, class TJ>
 static cudaError_t dcgs_dispatch(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                                 unsigned int* err, int nsm, cudaStream_t st) {
-  if (j < 8) return dcgs_launch_k<TB, TJ, 8>(pass, n, V, j, w, ctl, red, err, nsm, st);
-  if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st);
-  if (j < 24) return dcgs_launch_k<TB, TJ, 24>(pass, n, V, j, w, ctl, red, err, nsm, st);
-  if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st);
-  return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st);
+                                 unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
+  if (j < 8) return dcgs_launch_k<TB, TJ, 8>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+  if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+  if (j < 24) return dcgs_launch_k<TB, TJ, 24>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+  if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+  return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
 }
 
 }  // namespace jfnk

@@ -95,7 +95,7 @@ struct jfnk_ctx {
   RedWs red{};
   int red_cap_blocks = 0;
   // pinned / mapped host memory
-  volatile int* hflag = nullptr;  // mapped: mirror of the Krylov `active` flag
+  volatile int* hflag = nullptr;  // mapped: [0] mirror of the Krylov `active` flag, [1] delayed-CGS2 steps done
   int* hflag_dev = nullptr;       // its device address
   double* hbuf = nullptr;         // pinned read-back buffer (16 KB)
   cudaEvent_t iter_ev[kLookahead + 1] = {};
@@ -282,6 +282,13 @@ struct Solver {
   jfnk_status jvp(JvpArgs& a, int tag) {
     a.t = tj;
     a.err = ctx->derr;
+    if (a.precond && a.lin == 1 && o.fd_eps <= 0 && o.fd_rule == JFNK_EPS_SCALED) {
+      // the FD step of the preconditioned direction: ||M^-1 v|| in place of ||v|| (times the vector's scale)
+      cudaError_t e = launch_precond(P, tj, a.x, a.v, nullptr, ctx->dsc + 18, o.precond_damping, ctx->red,
+                                     ctx->stream);
+      if (e != cudaSuccess) return cuda_fail(ctx, e, "preconditioner norm kernel");
+      a.vn2 = ctx->dsc + 18;
+    }
     const double s = (double)sj();
     double bytes = (double)N * (s + vt_size(a.tv) + s) + aux_bytes(tj);     // x, v -> out
     if (a.lin == 1) bytes += (double)N * s;                                 // F(x)
@@ -308,7 +315,17 @@ struct Solver {
     a.eps_fixed = o.fd_eps;
     a.eps_rule = o.fd_rule;
     a.xn2 = sc + 1;
+    a.precond = o.precond == JFNK_PRECOND_CSLP ? 1 : 0;
+    a.pbeta = o.precond_damping;
     return a;
+  }
+
+  // ---- the Newton step from the right-preconditioned solve: d = M^-1 y (in place)
+  jfnk_status precond_solution() {
+    if (o.precond != JFNK_PRECOND_CSLP) return JFNK_OK;
+    cudaError_t e = launch_precond(P, td, x, ctx->ws.d, ctx->ws.d, nullptr, o.precond_damping, ctx->red, ctx->stream);
+    if (e != cudaSuccess) return cuda_fail(ctx, e, "preconditioner kernel");
+    return JFNK_OK;
   }
 
   jfnk_status cast(int ti, int to, const void* src, void* dst, double c) {
@@ -340,17 +357,44 @@ struct Solver {
     return JFNK_OK;
   }
 
+  // ---- wait until the device has completed `steps` delayed-CGS2 steps of the
+  // current cycle (mapped word host_active[1]) or stopped the cycle (word 0
+  // cleared). Bounded: after 2 s without either the host drains the stream,
+  // which always ends because every device wait is itself bounded.
+  jfnk_status wait_progress(int steps) {
+    const auto t0 = std::chrono::steady_clock::now();
+    for (long long spin = 0; ctx->hflag[1] < steps && ctx->hflag[0] != 0; ++spin) {
+      if ((spin & 1023) == 1023 && std::chrono::steady_clock::now() - t0 > std::chrono::seconds(2)) {
+        CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");
+        break;
+      }
+    }
+    return JFNK_OK;
+  }
+
   // ---- one cycle of delayed-CGS2 Arnoldi: candidate u_j in basis slot j,
   // JVP, fused dots (completes column j - 1), fused update (q_j, u_{j+1});
   // the dots of u_m complete the last column. The device clears `active`
   // when the cycle stops; kernels queued past that point return at once.
+  // Without per-kernel timing the three kernels of a step are launched
+  // programmatically (PDL, stream.cuh), each dispatched while the one before
+  // it drains, and the host bounds its lookahead by the mapped word that the
+  // update pass advances (GmresCtl::host_active[1]) instead of by a stream
+  // event, which would sit between two kernels and serialise them.
   jfnk_status dcgs_cycle(int m, int* steps_run) {
     jfnk_ctx::Ws& w = ctx->ws;
     const double nv = (double)N;
+    const bool pdl = !ctx->tm.on;
+    ctx->hflag[1] = 0;
     int j = 0;
     for (; j < m; ++j) {
       if (j >= kLookahead) {
-        CK(cudaEventSynchronize(ctx->iter_ev[(j - kLookahead) % (kLookahead + 1)]), "iteration event");
+        if (pdl) {
+          jfnk_status s = wait_progress(j - kLookahead + 1);
+          if (s) return s;
+        } else {
+          CK(cudaEventSynchronize(ctx->iter_ev[(j - kLookahead) % (kLookahead + 1)]), "iteration event");
+        }
       }
       if (*ctx->hflag == 0) break;
       JvpArgs a = jvp_base();
@@ -359,23 +403,25 @@ struct Solver {
       a.vscale = ctx->gctl->scale + j;
       a.out = w.w;
       a.active = &ctx->gctl->active;
+      a.pdl = pdl ? 1 : 0;
       jfnk_status s = jvp(a, j);
       if (s) return s;
       const double bs = (double)(j + 1) * nv * sb();
       int ev1 = tm_begin(ctx, KC_DCGS1, bs + nv * sj(), j);
-      cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream);
+      cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream,
+                                  pdl);
       tm_end(ctx, ev1);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs dots kernel");
       int ev2 = tm_begin(ctx, KC_DCGS2, bs + nv * sj() + 2.0 * nv * sb(), j + 1);   // did work iff j < k
-      e = launch_dcgs(2, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream);
+      e = launch_dcgs(2, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream, pdl);
       tm_end(ctx, ev2);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs update kernel");
-      CK(cudaEventRecord(ctx->iter_ev[j % (kLookahead + 1)], ctx->stream), "event record");
+      if (!pdl) CK(cudaEventRecord(ctx->iter_ev[j % (kLookahead + 1)], ctx->stream), "event record");
     }
     if (j == m) {   // the last column of the cycle
       int ev1 = tm_begin(ctx, KC_DCGS1, (double)(m + 1) * nv * sb(), m);
       cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, m, nullptr, ctx->gctl, ctx->red, ctx->derr, ctx->nsm,
-                                  ctx->stream);
+                                  ctx->stream, !ctx->tm.on);
       tm_end(ctx, ev1);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs dots kernel");
     }
@@ -707,6 +753,8 @@ struct Solver {
       int kst = 0;
       s = (o.krylov == JFNK_BICGSTAB) ? bicgstab(&kst) : (o.krylov == JFNK_CG ? cg(&kst) : gmres(&kst));
       if (s) return s;
+      s = precond_solution();
+      if (s) return s;
       if (kst == JFNK_E_BREAKDOWN || kst == JFNK_E_NONFINITE) { *nstatus = kst; break; }
       if (kst == JFNK_E_NOT_CONVERGED) rep.krylov_failures += 1;
       // backtracking line search on ||F||, decided on the device (LsCtl): every trial
@@ -759,6 +807,7 @@ size_t workspace_estimate(const jfnk_problem* pr, const jfnk_opts* o) {
   if (o->krylov == JFNK_GMRES && tj == VT_F32 && tb == VT_F32) b += 3 * N * sj;   // fused Arnoldi buffers
   b += (size_t)2048 * kMaxK * 8 + 65536;   // reductions and control blocks
   if (pr->pde == JFNK_MAXWELL_TE2D) b += (size_t)pr->nx * pr->ny * 3 * 12;
+  if (pr->pde == JFNK_MAXWELL_VEC2D) b += (size_t)pr->nx * pr->ny * 4 * 12;
   return b;
 }
 }  // namespace jfnk
@@ -843,6 +892,8 @@ void jfnk_default_opts(jfnk_opts* o, int prec) {
   o->ls_min_alpha = 1.0 / 1024.0;
   o->born_start = 1;
   o->ortho = JFNK_CGS2;
+  o->precond = JFNK_PRECOND_NONE;
+  o->precond_damping = 0.5;
 }
 
 jfnk_status jfnk_create(jfnk_ctx** out, int device, size_t hbm_budget, void* cuda_stream) {
@@ -896,9 +947,9 @@ jfnk_status jfnk_set_problem(jfnk_ctx* ctx, const jfnk_problem* pr) {
   cudaFree(ctx->eps64); cudaFree(ctx->eps32); cudaFree(ctx->src64); cudaFree(ctx->src32);
   ctx->eps64 = nullptr; ctx->eps32 = nullptr; ctx->src64 = nullptr; ctx->src32 = nullptr;
   const long long n = P.ncell;
-  if (pde == JFNK_MAXWELL_TE2D) {
+  if (pde == JFNK_MAXWELL_TE2D || pde == JFNK_MAXWELL_VEC2D) {
     const double* hin[2] = {pr->aux[0], pr->aux[1]};
-    const long long cnt[2] = {n, 2 * n};
+    const long long cnt[2] = {n, pde_source_planes(pde) * n};
     double** d64[2] = {&ctx->eps64, &ctx->src64};
     float** d32[2] = {&ctx->eps32, &ctx->src32};
     for (int q = 0; q < 2; ++q) {
@@ -1004,6 +1055,16 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
   if (o->fd_rule != JFNK_EPS_SCALED && o->fd_rule != JFNK_EPS_PAPER) return fail(ctx, JFNK_E_INVALID, "bad fd_rule");
   if (o->ortho != JFNK_CGS2 && o->ortho != JFNK_DCGS2 && o->ortho != JFNK_DCGS2_FUSED)
     return fail(ctx, JFNK_E_INVALID, "bad ortho");
+  if (o->precond != JFNK_PRECOND_NONE && o->precond != JFNK_PRECOND_CSLP)
+    return fail(ctx, JFNK_E_INVALID, "bad precond");
+  if (o->precond == JFNK_PRECOND_CSLP) {
+    if (ctx->P.pde != JFNK_MAXWELL_VEC2D)
+      return fail(ctx, JFNK_E_INVALID, "the CSLP preconditioner belongs to the vector Maxwell problem");
+    if (o->krylov != JFNK_GMRES || o->prec == JFNK_MIXED_BF16 || o->ortho == JFNK_DCGS2_FUSED)
+      return fail(ctx, JFNK_E_INVALID, "the CSLP preconditioner needs GMRES with a CGS2 or delayed-CGS2 FP64/FP32 basis");
+    if (!(o->precond_damping >= 0.0 && std::isfinite(o->precond_damping)))
+      return fail(ctx, JFNK_E_INVALID, "bad precond_damping");
+  }
   if (o->krylov == JFNK_GMRES && o->ortho != JFNK_CGS2 && !(ctx->stream_ok && stream_supported(ctx->N)))
     return fail(ctx, JFNK_E_INVALID, "delayed CGS2 needs the streaming kernels (unknowns a multiple of 8)");
   if (o->krylov == JFNK_GMRES && o->ortho == JFNK_DCGS2_FUSED) {
@@ -1055,7 +1116,7 @@ jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_pre
   const size_t sbytes = (size_t)N * vt_size(sv.ts);
   if (ctx->P.bvp) {
     double denom = 0.0;
-    if (opts->born_start && ctx->P.pde == JFNK_MAXWELL_TE2D) {
+    if (opts->born_start && (ctx->P.pde == JFNK_MAXWELL_TE2D || ctx->P.pde == JFNK_MAXWELL_VEC2D)) {
       // Born start: the chi3 = 0 problem solved once from zero
       Solver lin = sv;
       lin.P.p1 = 0.0;

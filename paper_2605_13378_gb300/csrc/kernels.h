@@ -18,7 +18,13 @@ enum VType { VT_F64 = 0, VT_F32 = 1, VT_BF16 = 2 };
 inline size_t vt_size(int t) { return t == VT_F64 ? 8 : (t == VT_F32 ? 4 : 2); }
 // Fields per cell of a PDE (jfnk_pde).
 inline int pde_nfields(int pde) {
+  if (pde == JFNK_MAXWELL_VEC2D) return 4;
   return (pde == JFNK_SU_OLSON2D || pde == JFNK_MAXWELL_TE2D || pde == JFNK_BURGERS2D) ? 2 : 1;
+}
+// Planes of the source array aux[1] of a problem (Maxwell: Re, Im of f; the
+// vector form: Re J_x, Im J_x, Re J_y, Im J_y).
+inline int pde_source_planes(int pde) {
+  return pde == JFNK_MAXWELL_VEC2D ? 4 : (pde == JFNK_MAXWELL_TE2D ? 2 : 0);
 }
 
 // Device workspace of one reduction site (partials + arrival counter).
@@ -58,6 +64,12 @@ cudaError_t launch_residual(const ProbDev& P, int t, const void* x, const void* 
                             const void* b, void* F, void* xout, float* x32, RedWs red, double* sums,
                             cudaStream_t st, LsCtl* ls = nullptr);
 
+// The problem's right preconditioner at the state x (precision t): out =
+// M^-1(x) v node by node (out may equal v, or be null) and, when sums is set,
+// sums[0] = ||M^-1(x) v||^2. cudaErrorInvalidValue for a PDE without one.
+cudaError_t launch_precond(const ProbDev& P, int t, const void* x, const void* v, void* out, double* sums, double beta,
+                           RedWs red, cudaStream_t st);
+
 // b = M(xn) + (1 - theta) dt G(xn) in precision t.
 cudaError_t launch_rhs(const ProbDev& P, int t, const void* xn, void* b, cudaStream_t st);
 
@@ -83,6 +95,9 @@ struct JvpArgs {
   float* eps_out;              // FD: the step used (for reporting), may be null
   const int* active;           // device flag: the kernel does nothing when *active == 0 (null: always run)
   unsigned int* err;           // device error word for bounded waits of the staged sweep (null: not staged)
+  int pdl;                     // staged sweep: programmatic launch after the previous kernel in the stream
+  int precond;                 // the direction is M^-1 v (the problem's right preconditioner, gather form)
+  double pbeta;                // its damping
 };
 cudaError_t launch_jvp(const ProbDev& P, const JvpArgs& a, RedWs red, cudaStream_t st);
 

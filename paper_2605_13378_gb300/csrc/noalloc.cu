@@ -111,7 +111,7 @@ __global__ void __launch_bounds__(256) k_na_norms(long long n, const T* __restri
 // arrays are used in place (FP64 device pointers).
 static bool na_problem(const jfnk_problem* pr, ProbDev* P) {
   if (!make_probdev(pr, P, nullptr)) return false;
-  if (pr->pde == JFNK_MAXWELL_TE2D) {
+  if (pr->pde == JFNK_MAXWELL_TE2D || pr->pde == JFNK_MAXWELL_VEC2D) {
     P->eps64 = pr->aux[0];
     P->src64 = pr->aux[1];
   }
@@ -130,7 +130,8 @@ extern "C" jfnk_status jfnk_jvp_fd_noalloc(const jfnk_problem* prob, int prec, c
   ProbDev P;
   if (!na_problem(prob, &P)) return JFNK_E_INVALID;
   if (P.cfl > 0.0) return JFNK_E_INVALID;   // an adaptive step exists only inside jfnk_solve
-  if (P.pde == JFNK_MAXWELL_TE2D && prec != JFNK_FP64) return JFNK_E_INVALID;   // eps_r, source are FP64
+  if ((P.pde == JFNK_MAXWELL_TE2D || P.pde == JFNK_MAXWELL_VEC2D) && prec != JFNK_FP64)
+    return JFNK_E_INVALID;   // eps_r, source are FP64
   const int t = prec == JFNK_FP64 ? VT_F64 : VT_F32;
   const size_t es = prec == JFNK_FP64 ? 8 : 4;
   const long long N = P.ncell * P.nf;

@@ -81,11 +81,20 @@ struct Nb {
   V ne[NF], nw[NF], se[NF], sw[NF];
 };
 
-// Per-cell coefficients read from problem arrays (Maxwell: eps_r, source).
+// Per-cell coefficients read from problem arrays (Maxwell: eps_r, source;
+// the vector form's current: fr + i fi = J_x, gr + i gi = J_y).
 template <class T>
 struct CellAux {
-  T eps, fr, fi;
+  T eps, fr, fi, gr, gi;
 };
+
+// sqrt of a sum of squares with the derivative taken as 0 where the sum is 0
+// (|E| at a node where the field vanishes: the residual's branch there)
+template <class T> __device__ __forceinline__ Dual<T> sqrt0(Dual<T> s) {
+  return primal(s) > T(0) ? dsqrt(s) : Dual<T>(T(0), T(0));
+}
+__device__ __forceinline__ double sqrt0(double s) { return s > 0.0 ? sqrt(s) : 0.0; }
+__device__ __forceinline__ float sqrt0(float s) { return s > 0.0f ? sqrtf(s) : 0.0f; }
 
 // ---------------------------------------------------------------------------
 // 1D viscous Burgers, periodic, cells x_i = i/N. Conservative upwind flux
@@ -94,6 +103,8 @@ struct CellAux {
 //   G_i = -(Phi_{i+1/2} - Phi_{i-1/2}) / h + nu (u_{i+1} - 2u_i + u_{i-1}) / h^2
 // ---------------------------------------------------------------------------
 struct Burgers1D {
+  static constexpr bool PRECOND = false;
+  static constexpr int NSRC = 0;
   static constexpr int NF = 1;
   static constexpr bool DIAG = false;
   static constexpr int POLICY = BP_WRAP;
@@ -119,6 +130,8 @@ struct Burgers1D {
 // invhx, invhy are 1/hx, 1/hy of the square (not of the unit square).
 // ---------------------------------------------------------------------------
 struct Burgers2D {
+  static constexpr bool PRECOND = false;
+  static constexpr int NSRC = 0;
   static constexpr int NF = 2;
   static constexpr bool DIAG = false;
   static constexpr int POLICY = BP_WRAP;
@@ -147,6 +160,8 @@ struct Burgers2D {
 // nodes, so that a neighbour beyond a wall is 0.
 // ---------------------------------------------------------------------------
 struct AllenCahn2D {
+  static constexpr bool PRECOND = false;
+  static constexpr int NSRC = 0;
   static constexpr int NF = 1;
   static constexpr bool DIAG = false;
   static constexpr int POLICY = BP_WRAP;
@@ -180,6 +195,8 @@ struct AllenCahn2D {
 // The clamp policy supplies the mirror values.
 // ---------------------------------------------------------------------------
 struct SuOlson2D {
+  static constexpr bool PRECOND = false;
+  static constexpr int NSRC = 0;
   static constexpr int NF = 2;
   static constexpr bool DIAG = true;
   static constexpr int POLICY = BP_CLAMP;
@@ -241,6 +258,8 @@ struct SuOlson2D {
 // first-order absorbing condition dE/dn = i k E discretised at the wall.
 // ---------------------------------------------------------------------------
 struct MaxwellTE2D {
+  static constexpr bool PRECOND = false;
+  static constexpr int NSRC = 2;
   static constexpr int NF = 2;
   static constexpr bool DIAG = false;
   static constexpr int POLICY = BP_CLAMP;
@@ -266,6 +285,104 @@ struct MaxwellTE2D {
     M[1] = B;
     G[0] = LA + coef * A - aux.fr;
     G[1] = LB + coef * B - aux.fi;
+  }
+};
+
+// ---------------------------------------------------------------------------
+// The paper's vector TE Maxwell problem in a Kerr medium (App. A, Time-
+// Harmonic Maxwell's Equations in Kerr Media), as a real map on the planes
+// [Re E_x, Im E_x, Re E_y, Im E_y] = [a, b, c, d]:
+//   F = curl curl E - w^2 eps(E) E - i w J,
+//   eps(E) = (1 - L i)(1 + chi |E|),  |E| = sqrt(a^2 + b^2 + c^2 + d^2),
+// with L = p[2] (the paper's 0.05), w = p[0], chi = p[1], on nodes
+// x_i = i hx, hx = 1/(nx - 1) of the unit square whose walls are nodes.
+// Central differences: (curl curl E)_x = d2E_y/dxdy - d2E_x/dy2,
+// (curl curl E)_y = d2E_x/dxdy - d2E_y/dx2, the mixed derivative on the four
+// corner neighbours. Perfect electric conductor walls: the tangential
+// component's rows are F = E_t (E_x on the bottom and top walls, E_y on the
+// left and right ones); a neighbour beyond a wall is the image across it,
+// the tangential component odd and the normal one even (the corner beyond
+// two walls takes both signs). |E| = 0 takes a zero derivative.
+// ---------------------------------------------------------------------------
+struct MaxwellVec2D {
+  static constexpr bool PRECOND = true;
+  static constexpr int NSRC = 4;
+  static constexpr int NF = 4;
+  static constexpr bool DIAG = true;
+  static constexpr int POLICY = BP_CLAMP;
+  static constexpr bool AUX = true;
+  template <class T, class V>
+  __device__ __forceinline__ static void cell(const ProbDev& P, int i, int j, const Nb<V, 4>& q,
+                                              const CellAux<T>& aux, V* M, V* G) {
+    const int nx = P.nx, ny = P.ny;
+    const bool wx0 = i == 0, wx1 = i == nx - 1, wy0 = j == 0, wy1 = j == ny - 1;
+    V W[4], E[4], S[4], N[4], NE[4], NW[4], SE[4], SW[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      const T sx = f < 2 ? T(1) : T(-1);   // image across an x wall: E_x even, E_y odd
+      const T sy = f < 2 ? T(-1) : T(1);   // across a y wall: E_x odd, E_y even
+      W[f] = wx0 ? sx * q.e[f] : q.w[f];
+      E[f] = wx1 ? sx * q.w[f] : q.e[f];
+      S[f] = wy0 ? sy * q.n[f] : q.s[f];
+      N[f] = wy1 ? sy * q.s[f] : q.n[f];
+      // a corner beyond a wall is the image of the corner on the other side of that wall
+      const V ne = wx1 ? (wy1 ? q.sw[f] : q.nw[f]) : (wy1 ? q.se[f] : q.ne[f]);
+      const V nw = wx0 ? (wy1 ? q.se[f] : q.ne[f]) : (wy1 ? q.sw[f] : q.nw[f]);
+      const V se = wx1 ? (wy0 ? q.nw[f] : q.sw[f]) : (wy0 ? q.ne[f] : q.se[f]);
+      const V sw = wx0 ? (wy0 ? q.ne[f] : q.se[f]) : (wy0 ? q.nw[f] : q.sw[f]);
+      NE[f] = (wx1 ? sx : T(1)) * (wy1 ? sy : T(1)) * ne;
+      NW[f] = (wx0 ? sx : T(1)) * (wy1 ? sy : T(1)) * nw;
+      SE[f] = (wx1 ? sx : T(1)) * (wy0 ? sy : T(1)) * se;
+      SW[f] = (wx0 ? sx : T(1)) * (wy0 ? sy : T(1)) * sw;
+    }
+    const T ihx2 = T(P.invhx2), ihy2 = T(P.invhy2), ixy = T(0.25) * T(P.invhx) * T(P.invhy);
+    V cc[4], dyy[4], dxx[4], dxy[4];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+      cc[f] = q.c[f];
+      dyy[f] = (N[f] - T(2) * cc[f] + S[f]) * ihy2;
+      dxx[f] = (E[f] - T(2) * cc[f] + W[f]) * ihx2;
+      dxy[f] = (NE[f] - SE[f] - NW[f] + SW[f]) * ixy;
+    }
+    const V a = cc[0], b = cc[1], c = cc[2], d = cc[3];
+    const V m = sqrt0(a * a + b * b + c * c + d * d);
+    const V e = T(1) + T(P.p1) * m;
+    const T w = T(P.p0), w2 = w * w, L = T(P.p2);
+    V F0 = (dxy[2] - dyy[0]) - w2 * e * (a + L * b) + w * aux.fi;
+    V F1 = (dxy[3] - dyy[1]) - w2 * e * (b - L * a) - w * aux.fr;
+    V F2 = (dxy[0] - dxx[2]) - w2 * e * (c + L * d) + w * aux.gi;
+    V F3 = (dxy[1] - dxx[3]) - w2 * e * (d - L * c) - w * aux.gr;
+    if (wy0 || wy1) { F0 = a; F1 = b; }   // PEC: E_x tangential to the bottom and top walls
+    if (wx0 || wx1) { F2 = c; F3 = d; }   // PEC: E_y tangential to the left and right walls
+    M[0] = a; M[1] = b; M[2] = c; M[3] = d;
+    G[0] = F0; G[1] = F1; G[2] = F2; G[3] = F3;
+  }
+  // The paper's block-diagonal complex-shifted-Laplacian preconditioner (App.
+  // A, Preconditioning) at node (i, j) with the field x there: v is replaced
+  // by M^-1 v, the x and y components divided by
+  //   M_xx = 2/hy^2 - w^2 eps_p,  M_yy = 2/hx^2 - w^2 eps_p,
+  //   eps_p = eps(E)(1 - beta i) = (1 - L i)(1 - beta i)(1 + chi |E|),
+  // and left alone on the rows of tangential components on the walls (M = 1,
+  // those Jacobian rows being the identity).
+  template <class T>
+  __device__ __forceinline__ static void precond(const ProbDev& P, T beta, int i, int j, const T* x, T* v) {
+    const T m = sqrt0(x[0] * x[0] + x[1] * x[1] + x[2] * x[2] + x[3] * x[3]);
+    const T e = T(1) + T(P.p1) * m, L = T(P.p2), w2 = T(P.p0) * T(P.p0);
+    const T er = e * (T(1) - L * beta), ei = -e * (L + beta);   // eps_p = er + i ei
+    const T mi = -w2 * ei;
+    const bool pec_x = (j == 0 || j == P.ny - 1), pec_y = (i == 0 || i == P.nx - 1);
+    if (!pec_x) {   // (v0 + i v1) / (mxr + i mi)
+      const T mr = T(2) * T(P.invhy2) - w2 * er, den = mr * mr + mi * mi;
+      const T a = v[0], b = v[1];
+      v[0] = (a * mr + b * mi) / den;
+      v[1] = (b * mr - a * mi) / den;
+    }
+    if (!pec_y) {
+      const T mr = T(2) * T(P.invhx2) - w2 * er, den = mr * mr + mi * mi;
+      const T a = v[2], b = v[3];
+      v[2] = (a * mr + b * mi) / den;
+      v[3] = (b * mr - a * mi) / den;
+    }
   }
 };
 

@@ -38,7 +38,7 @@ jfnk_status Server::submit(const jfnk_problem* prob, const jfnk_opts* opts, cons
   const long long cells = (long long)prob->nx * prob->ny *
                           pde_nfields(prob->pde);
   const bool batched = cells <= batch_max_cells_ && BatchEngine::supports(prob, opts, nullptr) &&
-                       (prob->pde == JFNK_MAXWELL_TE2D || steps >= 1);
+                       (prob->pde == JFNK_MAXWELL_TE2D || prob->pde == JFNK_MAXWELL_VEC2D || steps >= 1);
   const size_t need = batched ? BatchEngine::workspace_bytes(prob, opts) : workspace_estimate(prob, opts);
   if (need == 0) return JFNK_E_INVALID;
   if (budget_ && need > budget_) return JFNK_E_OOM;

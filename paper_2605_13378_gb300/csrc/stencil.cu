@@ -39,6 +39,7 @@ static cudaError_t stencil_pde(int mode, const ProbDev& P, int t, int tv, const 
     case 2: return stencil_su_olson(mode, P, t, tv, a, red, st);
     case 3: return stencil_maxwell(mode, P, t, tv, a, red, st);
     case 4: return stencil_burgers2d(mode, P, t, tv, a, red, st);
+    case 5: return stencil_maxwell_vec(mode, P, t, tv, a, red, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -50,6 +51,14 @@ cudaError_t launch_residual(const ProbDev& P, int t, const void* x, const void* 
   memset(&a, 0, sizeof(a));
   a.x = x; a.v = d; a.alpha = alpha; a.b = b; a.F = F; a.xout = xout; a.x32 = x32; a.sums = sums; a.ls = ls;
   return stencil_pde(SM_RESID, P, t, t, a, red, st);
+}
+
+cudaError_t launch_precond(const ProbDev& P, int t, const void* x, const void* v, void* out, double* sums, double beta,
+                           RedWs red, cudaStream_t st) {
+  StencilArgs a;
+  memset(&a, 0, sizeof(a));
+  a.x = x; a.v = v; a.out = out; a.sums = sums; a.pbeta = beta;
+  return stencil_pde(SM_PREC, P, t, t, a, red, st);
 }
 
 cudaError_t launch_rhs(const ProbDev& P, int t, const void* xn, void* b, cudaStream_t st) {
@@ -69,6 +78,9 @@ cudaError_t launch_jvp(const ProbDev& P, const JvpArgs& in, RedWs red, cudaStrea
   a.eps_fixed = in.eps_fixed; a.eps_rule = in.eps_rule; a.xn2 = in.xn2; a.vn2 = in.vn2; a.eps_out = in.eps_out;
   a.active = in.active;
   a.err = in.err;
+  a.pdl = in.pdl;
+  a.precond = in.precond;
+  a.pbeta = in.pbeta;
   if (in.lin == 0) return stencil_pde(SM_AD, P, in.t, in.tv, a, red, st);
   return stencil_pde(SM_FD, P, in.t, in.tv, a, red, st);
 }

@@ -26,7 +26,7 @@
 
 namespace jfnk {
 
-enum StencilMode { SM_RESID = 0, SM_RHS = 1, SM_AD = 2, SM_FD = 3 };
+enum StencilMode { SM_RESID = 0, SM_RHS = 1, SM_AD = 2, SM_FD = 3, SM_PREC = 4 };
 
 struct StencilArgs {
   const void* x;            // state (T)
@@ -54,6 +54,9 @@ struct StencilArgs {
   const int* active;
   LsCtl* ls;                // RESID: a line-search trial, alpha from ls->alpha (see LsCtl)
   unsigned int* err;        // AD, FD: device error word of the staged form's bounded waits (null: march form)
+  int pdl;                  // staged form: launched programmatically after the previous kernel
+  int precond;              // AD, FD: the direction is M^-1 v (PDE::precond at each node; gather form)
+  double pbeta;             // damping beta of the preconditioner
 };
 
 template <class T> struct AccOf { typedef float type; };
@@ -197,12 +200,13 @@ __device__ __forceinline__ void finish_reduction(const StencilArgs& a, Acc* acc,
 template <class PDE, class T>
 __device__ __forceinline__ CellAux<T> load_aux(const ProbDev& P, long long c) {
   CellAux<T> aux;
-  aux.eps = T(1); aux.fr = T(0); aux.fi = T(0);
+  aux.eps = T(1); aux.fr = T(0); aux.fi = T(0); aux.gr = T(0); aux.gi = T(0);
   if (PDE::AUX) {
     const T* ep = eps_of<T>(P);
     const T* sp = src_of<T>(P);
     if (ep) aux.eps = __ldg(ep + c);
     if (sp) { aux.fr = __ldg(sp + c); aux.fi = __ldg(sp + P.ncell + c); }
+    if (sp && PDE::NSRC >= 4) { aux.gr = __ldg(sp + 2 * P.ncell + c); aux.gi = __ldg(sp + 3 * P.ncell + c); }
   }
   return aux;
 }
@@ -243,6 +247,33 @@ __global__ void __launch_bounds__(256) k_gather(ProbDev P, int R, StencilArgs a,
       const T vv = v ? (T)ldv1(v, id) : T(0);
       return cb(xv, vv);
     };
+    if constexpr (PDE::PRECOND && (MODE == SM_AD || MODE == SM_FD)) {
+      if (a.precond) {
+        // every field of a node at once: the direction there becomes M^-1 v before it meets x
+        auto node = [&](int ii, int jj, V* dst, int stride) {
+          const long long cid = (long long)jj * P.nx + ii;
+          T xv[NF], vv[NF];
+#pragma unroll
+          for (int f = 0; f < NF; ++f) {
+            xv[f] = __ldg(x + f * P.ncell + cid);
+            vv[f] = (T)ldv1(v, f * P.ncell + cid);
+          }
+          PDE::precond(P, T(a.pbeta), ii, jj, xv, vv);
+#pragma unroll
+          for (int f = 0; f < NF; ++f) dst[f * stride] = cb(xv[f], vv[f]);
+        };
+        node(i, j, q.c, 1); node(ie, j, q.e, 1); node(iw, j, q.w, 1); node(i, jn, q.n, 1); node(i, js, q.s, 1);
+        if (PDE::DIAG) {
+          node(ie, jn, q.ne, 1); node(iw, jn, q.nw, 1); node(ie, js, q.se, 1); node(iw, js, q.sw, 1);
+        }
+        const long long c = (long long)j * P.nx + i;
+        const CellAux<T> aux = load_aux<PDE, T>(P, c);
+        V M[NF], G[NF];
+        PDE::template cell<T, V>(P, i, j, q, aux, M, G);
+        emit<MODE, PDE, T, V, Acc>(P, a, c, M, G, q.c, eps, acc);
+        continue;
+      }
+    }
 #pragma unroll
     for (int f = 0; f < NF; ++f) {
       const long long base = f * P.ncell;
@@ -267,6 +298,41 @@ __global__ void __launch_bounds__(256) k_gather(ProbDev P, int R, StencilArgs a,
     emit<MODE, PDE, T, V, Acc>(P, a, c, M, G, q.c, eps, acc);
   }
   finish_reduction<MODE, Acc>(a, acc, gridDim.x * gridDim.y, blockIdx.y * gridDim.x + blockIdx.x, red);
+}
+
+// --------------------------------------------------------------------------
+// the right preconditioner alone, node by node: out = M^-1(x) v (out may be
+// v itself or null) and, when sums is set, sums[0] = ||M^-1(x) v||^2
+// --------------------------------------------------------------------------
+template <class PDE, class T>
+__global__ void __launch_bounds__(256) k_precond(ProbDev P, StencilArgs a, RedSite<typename AccOf<T>::type> red) {
+  typedef typename AccOf<T>::type Acc;
+  constexpr int NF = PDE::NF;
+  const T* __restrict__ x = (const T*)a.x;
+  const T* v = (const T*)a.v;
+  T* out = (T*)a.out;
+  Acc acc[3] = {Acc(0), Acc(0), Acc(0)};
+  const long long stride = (long long)gridDim.x * blockDim.x;
+  for (long long c = (long long)blockIdx.x * blockDim.x + threadIdx.x; c < P.ncell; c += stride) {
+    T xv[NF], vv[NF];
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      xv[f] = x[f * P.ncell + c];
+      vv[f] = v[f * P.ncell + c];
+    }
+    if constexpr (PDE::PRECOND) PDE::precond(P, T(a.pbeta), (int)(c % P.nx), (int)(c / P.nx), xv, vv);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      if (out) out[f * P.ncell + c] = vv[f];
+      acc[0] += (Acc)vv[f] * (Acc)vv[f];
+    }
+  }
+  if (a.sums) {
+    __shared__ Acc sm[8 * 3];
+    Acc v3[3] = {acc[0], Acc(0), Acc(0)};
+    double* sums = a.sums;
+    grid_reduce<Acc, 3>(v3, 1, red, gridDim.x, blockIdx.x, sm, [&](int, Acc sv) { sums[0] = (double)sv; });
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -552,6 +618,8 @@ static int g_no_march = -1;   // JFNK_NO_MARCH=1 forces the gather form (testing
 
 template <class T, class TV>
 static bool march_ok(const ProbDev& P, const StencilArgs& a) {
+  if (P.nf > 2) return false;   // four planes: the register rows would spill; the gather form serves them
+  if (a.precond) return false;  // the preconditioned direction is formed per node in the gather form
   if (g_no_march < 0) {
     const char* e = getenv("JFNK_NO_MARCH");
     g_no_march = (e && e[0] == '1') ? 1 : 0;
@@ -570,33 +638,39 @@ template <class PDE, class T, class TV, int MODE>
 static cudaError_t stencil_launch(const ProbDev& P, const StencilArgs& a, RedWs red, cudaStream_t st) {
   typedef typename AccOf<T>::type Acc;
   RedSite<Acc> rs{(Acc*)red.partials, red.counter, red.max_blocks};
-  if (march_ok<T, TV>(P, a)) {
-    constexpr int VEC = 16 / (int)sizeof(T);
-    const MarchGeom g = march_geom(P, VEC);
-    // the plain Krylov product (no F, no addend, no reduction, unit factor) has a vector epilogue
-    if constexpr (MODE == SM_AD || MODE == SM_FD) {
-      // the plain Krylov product (no F, no addend, no reduction, unit factor) has a vector epilogue
-      const bool plain = !a.F && !a.add && a.ndots == 0 && a.c_jv == 1.0 && aligned(a.out, 16) &&
-                         (MODE != SM_FD || (aligned(a.Fx, 16) && aligned(a.b, 16)));
-      if (plain) {
-        // large 2D grids: rows staged in shared memory by bulk copies (stencil_stage.cuh)
-        StagePlan sp;
-        if (a.err && P.nx >= kStageWarps * 32 * VEC && P.ny >= 64 && aligned(a.v, 16) &&
-            stage_plan<T, TV, PDE::NF>(P, num_sms(), &sp)) {
-          static SmemOptIn opt_in;
-          cudaError_t e = smem_opt_in(k_jvp_stage<PDE, T, TV, MODE>, opt_in, sp.smem);
-          if (e != cudaSuccess) return e;
-          k_jvp_stage<PDE, T, TV, MODE><<<sp.grid, kStageThreads, sp.smem, st>>>(P, a, sp);
+  if constexpr (MODE == SM_PREC) {
+    if (!PDE::PRECOND) return cudaErrorInvalidValue;
+    k_precond<PDE, T><<<vec_blocks(P.ncell), 256, 0, st>>>(P, a, rs);
+  } else {
+    if (march_ok<T, TV>(P, a)) {
+      constexpr int VEC = 16 / (int)sizeof(T);
+      const MarchGeom g = march_geom(P, VEC);
+      if constexpr (MODE == SM_AD || MODE == SM_FD) {
+        // the plain Krylov product (no F, no addend, no reduction, unit factor) has a vector epilogue
+        const bool plain = !a.F && !a.add && a.ndots == 0 && a.c_jv == 1.0 && aligned(a.out, 16) &&
+                           (MODE != SM_FD || (aligned(a.Fx, 16) && aligned(a.b, 16)));
+        if (plain) {
+          // large 2D grids: rows staged in shared memory by bulk copies (stencil_stage.cuh)
+          StagePlan sp;
+          if (a.err && P.nx >= kStageWarps * 32 * VEC && P.ny >= 64 && aligned(a.v, 16) &&
+              stage_plan<T, TV, PDE::NF>(P, num_sms(), &sp)) {
+            static SmemOptIn opt_in;
+            cudaError_t e = smem_opt_in(k_jvp_stage<PDE, T, TV, MODE>, opt_in, sp.smem);
+            if (e != cudaSuccess) return e;
+            e = launch_maybe_pdl(a.pdl != 0, k_jvp_stage<PDE, T, TV, MODE>, dim3(sp.grid), dim3(kStageThreads),
+                                 (size_t)sp.smem, st, P, a, sp);
+            if (e != cudaSuccess) return e;
+            return cudaGetLastError();
+          }
+          k_march<PDE, T, TV, VEC, MODE, 1><<<g.nblocks, 256, 0, st>>>(P, g.nstrips, g.R, a, rs);
           return cudaGetLastError();
         }
-        k_march<PDE, T, TV, VEC, MODE, 1><<<g.nblocks, 256, 0, st>>>(P, g.nstrips, g.R, a, rs);
-        return cudaGetLastError();
       }
+      k_march<PDE, T, TV, VEC, MODE, 0><<<g.nblocks, 256, 0, st>>>(P, g.nstrips, g.R, a, rs);
+    } else {
+      const StencilGeom g = stencil_geom(P);
+      k_gather<PDE, T, TV, MODE><<<g.grid, g.block, 0, st>>>(P, g.rows_per_thread, a, rs);
     }
-    k_march<PDE, T, TV, VEC, MODE, 0><<<g.nblocks, 256, 0, st>>>(P, g.nstrips, g.R, a, rs);
-  } else {
-    const StencilGeom g = stencil_geom(P);
-    k_gather<PDE, T, TV, MODE><<<g.grid, g.block, 0, st>>>(P, g.rows_per_thread, a, rs);
   }
   return cudaGetLastError();
 }
@@ -624,6 +698,7 @@ cudaError_t stencil_dispatch(int mode, const ProbDev& P, int t, int tv, const St
     case SM_RHS: return stencil_types<PDE, SM_RHS>(P, t, tv, a, red, st);
     case SM_AD: return stencil_types<PDE, SM_AD>(P, t, tv, a, red, st);
     case SM_FD: return stencil_types<PDE, SM_FD>(P, t, tv, a, red, st);
+    case SM_PREC: return stencil_types<PDE, SM_PREC>(P, t, tv, a, red, st);
   }
   return cudaErrorInvalidValue;
 }
@@ -637,5 +712,7 @@ cudaError_t stencil_maxwell(int mode, const ProbDev& P, int t, int tv, const Ste
                             cudaStream_t st);
 cudaError_t stencil_burgers2d(int mode, const ProbDev& P, int t, int tv, const StencilArgs& a, RedWs red,
                               cudaStream_t st);
+cudaError_t stencil_maxwell_vec(int mode, const ProbDev& P, int t, int tv, const StencilArgs& a, RedWs red,
+                                cudaStream_t st);
 
 }  // namespace jfnk

@@ -28,7 +28,8 @@ namespace jfnk {
 constexpr int kStageWarps = 8;                        // consumer warps (warp 0 produces)
 constexpr int kStageThreads = 32 * (kStageWarps + 1);
 constexpr int kStageMaxSlots = 24;
-constexpr int kStageRingBytes = 96 * 1024;            // per CTA: two CTAs per SM
+constexpr int kStageRingBytes3 = 64 * 1024;           // ring per CTA at three CTAs per SM ...
+constexpr int kStageRingBytes2 = 96 * 1024;           // ... or at two, when 64 KB holds fewer than 6 slots
 constexpr int kStageMinRows = 4;                      // shortest band (two halo rows per band)
 
 // Launch plan of the staged sweep, computed on the host.
@@ -43,6 +44,17 @@ struct StagePlan {
   int offv;         // byte offset of the v rows inside a slot
   int grid;
   int smem;         // dynamic shared memory: slots and their full/empty barriers
+  int per_sm;       // CTAs per SM the ring is sized for
+};
+
+// Position in the ring: slot index and the parity of its current fill,
+// advanced without divisions.
+struct RingPos {
+  int slot;
+  uint32_t phase;
+  __device__ __forceinline__ void next(int slots) {
+    if (++slot == slots) { slot = 0; phase ^= 1u; }
+  }
 };
 
 template <class T, class TV, int NF>
@@ -55,10 +67,15 @@ inline bool stage_plan(const ProbDev& P, int nsm, StagePlan* g) {
   const int xrow = (g->W + 2 * HX) * (int)sizeof(T), vrow = (g->W + 2 * HV) * (int)sizeof(TV);
   g->offv = NF * xrow;
   g->slot_bytes = (NF * (xrow + vrow) + 127) / 128 * 128;
-  g->slots = kStageRingBytes / g->slot_bytes;
+  g->per_sm = 3;
+  g->slots = kStageRingBytes3 / g->slot_bytes;
+  if (g->slots < 6) {
+    g->per_sm = 2;
+    g->slots = kStageRingBytes2 / g->slot_bytes;
+  }
   if (g->slots > kStageMaxSlots) g->slots = kStageMaxSlots;
   if (g->slots < 4) return false;                     // three rows in use and one in flight at least
-  const int ctas = 2 * (nsm > 0 ? nsm : 1);
+  const int ctas = g->per_sm * (nsm > 0 ? nsm : 1);
   int nb = (ctas + g->nstrips - 1) / g->nstrips;
   int R = (P.ny + nb - 1) / nb;
   if (R < kStageMinRows) R = kStageMinRows;
@@ -90,15 +107,16 @@ __device__ __forceinline__ StageUnit stage_unit(const StagePlan& g, int u, int n
 template <class T, class TV, int NF, int POL>
 __device__ __forceinline__ bool stage_produce_unit(const ProbDev& P, const StagePlan& g, const StageUnit& su,
                                                    const T* x, const TV* v, unsigned char* sring, uint64_t* full,
-                                                   uint64_t* empty, long long* q, unsigned int* err, int* s_abort) {
+                                                   uint64_t* empty, RingPos* pos, int* filled, unsigned int* err,
+                                                   int* s_abort) {
   constexpr int HX = 16 / (int)sizeof(T), HV = 16 / (int)sizeof(TV);
   const int lane = threadIdx.x & 31;
   const int nx = P.nx;
   const uint32_t bytes = (uint32_t)NF * ((su.Wu + 2 * HX) * (uint32_t)sizeof(T) + (su.Wu + 2 * HV) * (uint32_t)sizeof(TV));
-  for (int r = su.j0 - 1; r <= su.j1; ++r, ++*q) {
-    const int slot = (int)(*q % g.slots);
-    if (*q >= g.slots &&
-        !mbar_wait_bounded(&empty[slot], (uint32_t)(((*q / g.slots) - 1) & 1), kWaitLimitNs)) {
+  for (int r = su.j0 - 1; r <= su.j1; ++r, pos->next(g.slots), ++*filled) {
+    const int slot = pos->slot;
+    // a slot's k-th refill waits for the k-th release (empty phase k - 1)
+    if (*filled >= g.slots && !mbar_wait_bounded(&empty[slot], pos->phase ^ 1u, kWaitLimitNs)) {
       if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); *s_abort = 1; }
       return false;
     }
@@ -167,7 +185,7 @@ __device__ __forceinline__ void srow_load(Row<T, VEC>& r, const TS* row, int cl,
 }
 
 template <class PDE, class T, class TV, int MODE>
-__global__ void __launch_bounds__(kStageThreads, 2)
+__global__ void __launch_bounds__(kStageThreads, 3)
     k_jvp_stage(ProbDev P, StencilArgs a, StagePlan g) {
   typedef Comb<MODE, T> CB;
   typedef typename CB::V V;
@@ -175,6 +193,8 @@ __global__ void __launch_bounds__(kStageThreads, 2)
   constexpr int POL = PDE::POLICY;
   constexpr int VEC = 16 / (int)sizeof(T);
   constexpr int HX = 16 / (int)sizeof(T), HV = 16 / (int)sizeof(TV);
+  grid_dep_wait();      // the kernel that wrote v (and the active flag) has completed (programmatic launch)
+  grid_dep_trigger();
   if (a.active && *a.active == 0) return;
   unsigned int* err = a.err;
   extern __shared__ __align__(128) unsigned char sring[];
@@ -196,43 +216,43 @@ __global__ void __launch_bounds__(kStageThreads, 2)
   const CB cb = make_comb<MODE, T>(0.0, s, eps);
   const int nx = P.nx, ny = P.ny;
   if (warp == 0) {
-    long long q = 0;
-    int u = blockIdx.x;
-    for (; u < g.units; u += gridDim.x) {
+    RingPos pos{0, 0u};
+    int filled = 0;
+    for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
       const StageUnit su = stage_unit(g, u, nx, ny);
-      if (!stage_produce_unit<T, TV, NF, POL>(P, g, su, (const T*)a.x, (const TV*)a.v, sring, full, empty, &q,
-                                               err, &s_abort))
+      if (!stage_produce_unit<T, TV, NF, POL>(P, g, su, (const T*)a.x, (const TV*)a.v, sring, full, empty, &pos,
+                                               &filled, err, &s_abort))
         break;
     }
     if (s_abort && lane == 0) {   // drain the copies still in flight before the CTA exits
       const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
-      for (long long r = (q - g.slots > 0 ? q - g.slots : 0); r < q; ++r)
+      for (long long r = (filled - g.slots > 0 ? filled - g.slots : 0); r < filled; ++r)
         mbar_wait_until(&full[r % g.slots], (uint32_t)((r / g.slots) & 1), deadline);
     }
     return;
   }
   const int cl = ((warp - 1) * 32 + lane) * VEC;   // this thread's first column inside the strip
   const T thdt = T(P.thdt);
-  long long q = 0;
+  RingPos ps{0, 0u};                               // slot of row j - 1 (rows j, j + 1 follow it)
   for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
     const StageUnit su = stage_unit(g, u, nx, ny);
     const bool act = cl < su.Wu;
     const int col = su.col0 + cl;
-    const int rows = su.j1 - su.j0;            // rows of the unit; slots q .. q + rows + 1
-    bool ok = true;
-    for (int t = 0; t < 2 && ok; ++t) {
-      const long long r = q + t;
-      ok = mbar_wait_bounded(&full[r % g.slots], (uint32_t)((r / g.slots) & 1), kWaitLimitNs);
-    }
+    const int rows = su.j1 - su.j0;            // rows of the unit; it fills rows + 2 slots
+    RingPos pc = ps;
+    pc.next(g.slots);
+    RingPos pn = pc;
+    pn.next(g.slots);
+    bool ok = mbar_wait_bounded(&full[ps.slot], ps.phase, kWaitLimitNs) &&
+              mbar_wait_bounded(&full[pc.slot], pc.phase, kWaitLimitNs);
     for (int jj = 0; jj < rows && ok; ++jj) {
-      const long long qs = q + jj, qc = qs + 1, qn = qs + 2;
-      ok = mbar_wait_bounded(&full[qn % g.slots], (uint32_t)((qn / g.slots) & 1), kWaitLimitNs);
+      ok = mbar_wait_bounded(&full[pn.slot], pn.phase, kWaitLimitNs);
       if (!ok) break;
       const int j = su.j0 + jj;
       if (act) {
-        const unsigned char* ss = sring + (size_t)(qs % g.slots) * g.slot_bytes;
-        const unsigned char* sc = sring + (size_t)(qc % g.slots) * g.slot_bytes;
-        const unsigned char* sn = sring + (size_t)(qn % g.slots) * g.slot_bytes;
+        const unsigned char* ss = sring + (size_t)ps.slot * g.slot_bytes;
+        const unsigned char* sc = sring + (size_t)pc.slot * g.slot_bytes;
+        const unsigned char* sn = sring + (size_t)pn.slot * g.slot_bytes;
         Row<T, VEC> xs[NF], xc[NF], xn[NF], vs[NF], vc[NF], vn[NF];
 #pragma unroll
         for (int f = 0; f < NF; ++f) {
@@ -307,7 +327,10 @@ __global__ void __launch_bounds__(kStageThreads, 2)
         }
       }
       __syncwarp();
-      if (lane == 0) mbar_arrive(&empty[qs % g.slots]);
+      if (lane == 0) mbar_arrive(&empty[ps.slot]);
+      ps = pc;
+      pc = pn;
+      pn.next(g.slots);
     }
     if (!ok) {
       if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); s_abort = 1; }
@@ -315,10 +338,10 @@ __global__ void __launch_bounds__(kStageThreads, 2)
     }
     __syncwarp();
     if (lane == 0) {   // the unit's last two rows are no longer needed
-      mbar_arrive(&empty[(q + rows) % g.slots]);
-      mbar_arrive(&empty[(q + rows + 1) % g.slots]);
+      mbar_arrive(&empty[ps.slot]);
+      mbar_arrive(&empty[pc.slot]);
     }
-    q += rows + 2;
+    ps = pn;           // the next unit's first row follows them
   }
 }
 

@@ -79,6 +79,17 @@ __device__ __forceinline__ bool mbar_wait_until(uint64_t* bar, uint32_t parity, 
   }
 }
 
+// Programmatic dependent launch (PDL). A kernel launched with
+// launch_maybe_pdl(true, ...) may be dispatched while the kernel before it in
+// the stream is still running: grid_dep_wait() blocks until that kernel has
+// completed and its memory is visible (a no-op for an ordinary launch), and
+// grid_dep_trigger() lets the next kernel be dispatched before this one ends.
+// Every kernel that uses them waits before it reads anything an earlier
+// kernel wrote, and its grid fits the GPU in one wave, so a dispatched but
+// waiting CTA never holds resources a running CTA of the same grid needs.
+__device__ __forceinline__ void grid_dep_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+__device__ __forceinline__ void grid_dep_trigger() { asm volatile("griddepcontrol.launch_dependents;" ::: "memory"); }
+
 // Bulk copy global -> shared, completing `bytes` on `bar` (16-byte aligned
 // addresses, bytes a multiple of 16).
 __device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
@@ -111,6 +122,53 @@ inline cudaError_t smem_opt_in(K* kernel, SmemOptIn& f, int bytes) {
   if (e != cudaSuccess) return e;
   if (cached) f.done[dev].store(true, std::memory_order_release);
   return cudaSuccess;
+}
+
+// Dynamic shared memory a block of a kernel may use on the current device:
+// the device's opt-in limit per block less the kernel's static shared memory,
+// kept per device ordinal.
+struct SmemLimit {
+  std::atomic<int> bytes[kOptInDevices];
+};
+template <class K>
+inline cudaError_t smem_block_limit(K* kernel, SmemLimit& c, int* out) {
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return e;
+  const bool cached = dev >= 0 && dev < kOptInDevices;
+  if (cached) {
+    const int v = c.bytes[dev].load(std::memory_order_acquire);
+    if (v > 0) { *out = v; return cudaSuccess; }
+  }
+  int optin = 0;
+  e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev);
+  if (e != cudaSuccess) return e;
+  cudaFuncAttributes fa;
+  e = cudaFuncGetAttributes(&fa, kernel);
+  if (e != cudaSuccess) return e;
+  const int v = optin - (int)fa.sharedSizeBytes;
+  if (v <= 0) return cudaErrorInvalidValue;
+  if (cached) c.bytes[dev].store(v, std::memory_order_release);
+  *out = v;
+  return cudaSuccess;
+}
+
+// Launch `kernel`, with the programmatic stream serialization attribute when
+// pdl is set (see grid_dep_wait).
+template <class... KArgs, class... Args>
+inline cudaError_t launch_maybe_pdl(bool pdl, void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem,
+                                    cudaStream_t st, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = st;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = pdl ? 1 : 0;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
 }
 
 // Error codes written to the device error word.

@@ -26,6 +26,8 @@ JFNK_E_BREAKDOWN, JFNK_E_NONFINITE, JFNK_E_LINESEARCH, JFNK_E_TIMEOUT, JFNK_E_BU
 JFNK_AD, JFNK_FD = 0, 1
 JFNK_GMRES, JFNK_BICGSTAB, JFNK_CG = 0, 1, 2
 JFNK_BURGERS1D, JFNK_ALLEN_CAHN2D, JFNK_SU_OLSON2D, JFNK_MAXWELL_TE2D, JFNK_BURGERS2D = 0, 1, 2, 3, 4
+JFNK_MAXWELL_VEC2D = 5
+JFNK_PRECOND_NONE, JFNK_PRECOND_CSLP = 0, 1
 JFNK_FP64, JFNK_FP32, JFNK_MIXED_FP32, JFNK_MIXED_BF16 = 0, 1, 2, 3
 JFNK_EPS_SCALED, JFNK_EPS_PAPER = 0, 1
 JFNK_CGS2, JFNK_DCGS2, JFNK_DCGS2_FUSED = 0, 1, 2
@@ -46,7 +48,8 @@ class jfnk_opts(C.Structure):
     _fields_ = [("lin", C.c_int), ("krylov", C.c_int), ("prec", C.c_int), ("restart", C.c_int),
                 ("max_newton", C.c_int), ("max_krylov", C.c_int), ("tol_newton", C.c_double),
                 ("tol_krylov", C.c_double), ("fd_rule", C.c_int), ("fd_eps", C.c_double), ("ls_c1", C.c_double),
-                ("ls_min_alpha", C.c_double), ("born_start", C.c_int), ("ortho", C.c_int)]
+                ("ls_min_alpha", C.c_double), ("born_start", C.c_int), ("ortho", C.c_int), ("precond", C.c_int),
+                ("precond_damping", C.c_double)]
 
 
 class jfnk_report(C.Structure):
@@ -222,7 +225,7 @@ def jfnk_batch_stats(ctx: int, pde: int = 0, prec: int = 0, nx: int = 0, ny: int
 # --- small conveniences over the same calls ------------------------------------------------------
 
 PDE_IDS = {"burgers1d": JFNK_BURGERS1D, "allen_cahn": JFNK_ALLEN_CAHN2D, "su_olson": JFNK_SU_OLSON2D,
-           "maxwell": JFNK_MAXWELL_TE2D, "burgers2d": JFNK_BURGERS2D}
+           "maxwell": JFNK_MAXWELL_TE2D, "burgers2d": JFNK_BURGERS2D, "maxwell_vec": JFNK_MAXWELL_VEC2D}
 
 
 def make_problem(pde: str, nx: int, ny: int = 1, dt: float = 0.0, theta: float = 1.0, params=(),

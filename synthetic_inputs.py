@@ -163,6 +163,29 @@ def maxwell_point_source(nx: int, ny: int | None = None) -> np.ndarray:
     return f
 
 
+MAXWELL_VEC_SOURCES = ("gauss", "dipole")
+
+
+def maxwell_vec_source(nx: int, ny: int | None = None, kind: str = "gauss", sigma: float = 0.05,
+                       x0: float = 0.5, y0: float = 0.5, sep: float = 0.1) -> np.ndarray:
+    """The paper's applied currents J of the vector TE Maxwell problem on the node grid of the unit square
+    (x_i = i/(nx - 1)): planes [Re Jx, Im Jx, Re Jy, Im Jy] with J_y = 0 and a real J_x,
+      gauss:  J_x = exp(-((x - x0)^2 + (y - y0)^2) / (2 sigma^2)),
+      dipole: J_x = exp(-((x - x0)^2 + (y - y1)^2) / (2 sigma^2)) - exp(-((x - x0)^2 + (y - y2)^2) / (2 sigma^2)),
+    y1, y2 = y0 -+ sep. The paper does not give x0, the y's or sigma; these defaults are this build's reading."""
+    ny = nx if ny is None else ny
+    X, Y = np.meshgrid(np.arange(nx) / (nx - 1), np.arange(ny) / (ny - 1))
+    g = lambda yc: np.exp(-((X - x0) ** 2 + (Y - yc) ** 2) / (2.0 * sigma * sigma))
+    if kind == "gauss":
+        jx = g(y0)
+    elif kind == "dipole":
+        jx = g(y0 - sep) - g(y0 + sep)
+    else:
+        raise ValueError(kind)
+    z = np.zeros(nx * ny)
+    return np.concatenate([jx.reshape(-1), z, z, z])
+
+
 def maxwell_wavenumber(n: int, ppw: float = 10.0, eps_max: float = 4.0) -> float:
     """Wavenumber giving ``ppw`` cells per wavelength in the densest medium.
 

@@ -232,10 +232,10 @@ def test_invalid_problems_are_rejected(J, ctx):
 # FP64 cells and at least 64 rows runs the staged form: rows of x and v copied into shared memory by bulk
 # copies, one CTA per (strip, band) unit. These cases give ragged last strips (1028 = 1024 + 4 columns;
 # 3 strips of 512 + 4 in FP64), ragged last bands, both wall policies (wrap: Allen-Cahn, 2D Burgers;
-# clamp: radiation, Maxwell, Dirichlet walls) and, at 3072 x 408 (3 strips x 102 bands of 4 rows on 304
-# CTAs), CTAs that take a second unit.
+# clamp: radiation, Maxwell, Dirichlet walls) and, at 5120 x 368 (5 strips x 92 bands of 4 rows, 460 units on 456
+# CTAs at three per SM), CTAs that take a second unit.
 STAGED = [("allen_cahn", 1028, 70), ("su_olson", 1024, 66), ("maxwell", 1028, 64), ("burgers2d", 1024, 65),
-          ("rd_dirichlet", 1028, 67), ("allen_cahn", 3072, 408)]
+          ("rd_dirichlet", 1028, 67), ("allen_cahn", 5120, 368)]
 
 
 @pytest.mark.parametrize("name,nx,ny", STAGED)
