@@ -155,7 +155,14 @@ typedef struct {
   int lin;            /* jfnk_linearisation */
   int krylov;         /* jfnk_krylov */
   int prec;           /* jfnk_precision */
-  int restart;        /* GMRES restart length m, 1..JFNK_MAX_RESTART */
+  int restart;        /* GMRES restart length m, 1..JFNK_MAX_RESTART; 0: chosen by the library's
+                         autotuner, which solves the first Newton system of a problem class
+                         (PDE, grid, precision, linearisation, Arnoldi form) once with each of
+                         m = 10, 20, 30, 40, 60 to tol_krylov, times them, keeps the fastest
+                         that converged for that class on the context and uses its step (so
+                         the choice is made at equal tolerance, not equal iterates). Only
+                         jfnk_solve and the served slot workers; the batched entry points
+                         need m >= 1. */
   int max_newton;     /* Newton iterations per nonlinear solve */
   int max_krylov;     /* GMRES restart cycles; BiCGSTAB / CG iterations */
   double tol_newton;  /* Eq. 5 */
@@ -182,6 +189,8 @@ typedef struct {
   double ls_alpha[16];  /* jfnk_solve: the step alpha the line search accepted in each of the
                            first 16 Newton iterations of the last nonlinear solve (0: none);
                            the batched and served paths leave it 0 */
+  int restart_used;     /* jfnk_solve, GMRES: the restart length of the last Krylov solve (the
+                           autotuner's choice when opts.restart = 0) */
 } jfnk_report;
 
 /* Defaults of the paper for a precision (Sec. 3.3): tol_Newton 1e-6 / 1e-4,

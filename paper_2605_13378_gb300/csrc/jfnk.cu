@@ -13,6 +13,8 @@
 
 #include <algorithm>
 #include <chrono>
+#include <map>
+#include <tuple>
 #include <cmath>
 #include <cstdio>
 #include <cstdlib>
@@ -40,6 +42,12 @@ const char* kKClassNames[KC_COUNT] = {
     "arnoldi_dcgs_update", "cfl_dt", "arnoldi_dcgs_fused"};
 
 constexpr int kLookahead = 3;   // Arnoldi / BiCGSTAB steps the host may run ahead of the device
+
+// GMRES restart lengths the autotuner (opts.restart = 0) times on the first
+// Newton system of a problem class
+constexpr int kTuneRestarts[] = {10, 20, 30, 40, 60};
+constexpr int kTuneMaxRestart = 60;
+typedef std::tuple<int, int, int, int, int, int> TuneKey;   // pde, nx, ny, precision, linearisation, ortho
 
 struct Pending {
   int cls;
@@ -104,7 +112,7 @@ struct jfnk_ctx {
     long long N = 0; int prec = -1, m = 0, krylov = -1; bool ok = false;
     void *x = nullptr, *xt = nullptr, *xn = nullptr, *F = nullptr, *Ft = nullptr, *b = nullptr, *d = nullptr;
     void *x32 = nullptr, *x32t = nullptr, *F32 = nullptr, *b32 = nullptr;
-    void *rhsk = nullptr, *w = nullptr, *dj = nullptr, *V = nullptr;
+    void *rhsk = nullptr, *w = nullptr, *dj = nullptr, *V = nullptr, *dbest = nullptr;
     void *u2[2] = {nullptr, nullptr}, *w2 = nullptr;   // fused delayed-CGS2 pass: candidates, second w
     void *r = nullptr, *rhat = nullptr, *p = nullptr, *v = nullptr, *s = nullptr, *t = nullptr;
     void* user = nullptr;        // FP64 staging of user arrays
@@ -114,6 +122,7 @@ struct jfnk_ctx {
   void* jscratch = nullptr;       // F(x) for jfnk_jvp's FD quotient when F_out is null
   size_t jscratch_bytes = 0;
   Timer tm;
+  std::map<TuneKey, int> tuned_restart;   // restart length chosen per problem class (opts.restart = 0)
   jfnk::Server* server = nullptr;
   jfnk::BatchEngine* batch = nullptr;   // jfnk_solve_batch
 };
@@ -221,6 +230,7 @@ jfnk_status ensure_ws(jfnk_ctx* ctx, int prec, int m, int krylov) {
   AL(w.rhsk, N * sj); AL(w.w, N * sj); AL(w.dj, N * sj);
   if (krylov == JFNK_GMRES) {
     AL(w.V, (size_t)(m + 1) * N * sb);
+    AL(w.dbest, N * ss);   // the restart autotuner's best step so far
     if (tj == VT_F32 && tb == VT_F32) { AL(w.u2[0], N * sj); AL(w.u2[1], N * sj); AL(w.w2, N * sj); }
   } else {
     AL(w.r, N * sj); AL(w.rhat, N * sj); AL(w.p, N * sj); AL(w.v, N * sj); AL(w.s, N * sj); AL(w.t, N * sj);
@@ -484,6 +494,7 @@ struct Solver {
   jfnk_status gmres(int* kstatus) {
     jfnk_ctx::Ws& w = ctx->ws;
     const int m = o.restart;
+    rep.restart_used = m;
     const double nv = (double)N;
     const bool streamed = ctx->stream_ok && stream_supported(N);
     const bool fused = o.ortho == JFNK_DCGS2_FUSED;
@@ -610,6 +621,52 @@ struct Solver {
       if (head.converged) { rep.krylov_its += head.its; return JFNK_OK; }
       if (cycle == o.max_krylov - 1) { rep.krylov_its += head.its; *kstatus = JFNK_E_NOT_CONVERGED; return JFNK_OK; }
     }
+    return JFNK_OK;
+  }
+
+  // ---- GMRES with the restart length of the options, or -- opts.restart = 0 --
+  // the one the autotuner chose for this problem class. The first Newton system
+  // of a class is solved once per candidate length (kTuneRestarts), each to the
+  // requested tolerance, timed on the host around the synchronous cycles; the
+  // fastest candidate that converged (else the one with the smallest residual)
+  // is kept for the class on this context, and its step is used.
+  jfnk_status gmres_auto(int* kstatus) {
+    if (o.restart > 0 || o.krylov != JFNK_GMRES) return gmres(kstatus);
+    const TuneKey key{P.pde, P.nx, P.ny, o.prec, o.lin, o.ortho};
+    auto it = ctx->tuned_restart.find(key);
+    if (it != ctx->tuned_restart.end()) {
+      o.restart = it->second;
+      jfnk_status s = gmres(kstatus);
+      o.restart = 0;
+      return s;
+    }
+    int best_m = 0, best_st = 0;
+    double best_t = 0.0, best_res = 0.0;
+    for (int m : kTuneRestarts) {
+      o.restart = m;
+      const auto t0 = std::chrono::steady_clock::now();
+      int kst = 0;
+      jfnk_status s = gmres(&kst);
+      o.restart = 0;
+      if (s) return s;
+      const double t = std::chrono::duration<double>(std::chrono::steady_clock::now() - t0).count();
+      GmresCtl head;
+      std::memcpy(&head, ctx->hbuf, kGmresHeadBytes);   // the head of the candidate's last cycle
+      const bool conv = kst == 0, best_conv = best_m > 0 && best_st == 0;
+      const bool better = best_m == 0 || (conv && (!best_conv || t < best_t)) ||
+                          (!conv && !best_conv && head.resid < best_res);
+      if (better) {
+        best_m = m; best_st = kst; best_t = t; best_res = head.resid;
+        CK(cudaMemcpyAsync(ctx->ws.dbest, ctx->ws.d, (size_t)N * ss(), cudaMemcpyDeviceToDevice, ctx->stream),
+           "keep step");
+      }
+      if (kst == JFNK_E_NONFINITE) break;
+    }
+    CK(cudaMemcpyAsync(ctx->ws.d, ctx->ws.dbest, (size_t)N * ss(), cudaMemcpyDeviceToDevice, ctx->stream),
+       "best step");
+    ctx->tuned_restart[key] = best_m;
+    rep.restart_used = best_m;
+    *kstatus = best_st;
     return JFNK_OK;
   }
 
@@ -751,7 +808,7 @@ struct Solver {
         if (s) return s;
       }
       int kst = 0;
-      s = (o.krylov == JFNK_BICGSTAB) ? bicgstab(&kst) : (o.krylov == JFNK_CG ? cg(&kst) : gmres(&kst));
+      s = (o.krylov == JFNK_BICGSTAB) ? bicgstab(&kst) : (o.krylov == JFNK_CG ? cg(&kst) : gmres_auto(&kst));
       if (s) return s;
       s = precond_solution();
       if (s) return s;
@@ -803,7 +860,8 @@ size_t workspace_estimate(const jfnk_problem* pr, const jfnk_opts* o) {
   const size_t N = (size_t)pr->nx * pr->ny * nf;
   const size_t ss = vt_size(ts), sj = vt_size(tj), sb = vt_size(tb);
   size_t b = N * (7 * ss + 8 + 3 * sj) + (tj != ts ? 4 * N * sj : 0);
-  b += (o->krylov == JFNK_GMRES) ? (size_t)(o->restart + 1) * N * sb : 6 * N * sj;
+  const size_t m = o->restart > 0 ? (size_t)o->restart : (size_t)kTuneMaxRestart;
+  b += (o->krylov == JFNK_GMRES) ? (m + 1) * N * sb + N * ss : 6 * N * sj;
   if (o->krylov == JFNK_GMRES && tj == VT_F32 && tb == VT_F32) b += 3 * N * sj;   // fused Arnoldi buffers
   b += (size_t)2048 * kMaxK * 8 + 65536;   // reductions and control blocks
   if (pr->pde == JFNK_MAXWELL_TE2D) b += (size_t)pr->nx * pr->ny * 3 * 12;
@@ -1045,8 +1103,8 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
   if (o->lin != JFNK_AD && o->lin != JFNK_FD) return fail(ctx, JFNK_E_INVALID, "bad linearisation");
   if (o->krylov != JFNK_GMRES && o->krylov != JFNK_BICGSTAB && o->krylov != JFNK_CG)
     return fail(ctx, JFNK_E_INVALID, "krylov must be GMRES, BiCGSTAB or CG");
-  if (o->krylov == JFNK_GMRES && (o->restart < 1 || o->restart > JFNK_MAX_RESTART))
-    return fail(ctx, JFNK_E_INVALID, "restart out of range");
+  if (o->krylov == JFNK_GMRES && (o->restart < 0 || o->restart > JFNK_MAX_RESTART))
+    return fail(ctx, JFNK_E_INVALID, "restart out of range (0: tuned)");
   if (o->krylov != JFNK_GMRES && o->prec == JFNK_MIXED_BF16)
     return fail(ctx, JFNK_E_INVALID, "BF16 storage applies to the GMRES basis only");
   if (o->max_newton < 0 || o->max_krylov < 1) return fail(ctx, JFNK_E_INVALID, "bad iteration limits");
@@ -1069,7 +1127,7 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
     return fail(ctx, JFNK_E_INVALID, "delayed CGS2 needs the streaming kernels (unknowns a multiple of 8)");
   if (o->krylov == JFNK_GMRES && o->ortho == JFNK_DCGS2_FUSED) {
     const bool ok = o->lin == JFNK_AD && tb == VT_F32 && tj == VT_F32 && ctx->stream_ok &&
-                    dcgs_fused_supported(ctx->P, o->restart, ctx->nsm);
+                    dcgs_fused_supported(ctx->P, o->restart > 0 ? o->restart : kTuneMaxRestart, ctx->nsm);
     if (!ok)
       return fail(ctx, JFNK_E_INVALID, "the one-pass delayed CGS2 form needs the AD JVP, FP32 JVP and basis, and a "
                                        "2D problem with face neighbours only whose rows fit its shared-memory plan");
@@ -1086,7 +1144,7 @@ jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_pre
   if (!ctx->P.bvp && steps < 1) return fail(ctx, JFNK_E_INVALID, "steps must be >= 1");
   const auto t0 = std::chrono::steady_clock::now();
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
-  s = ensure_ws(ctx, opts->prec, opts->restart, opts->krylov);
+  s = ensure_ws(ctx, opts->prec, opts->restart > 0 ? opts->restart : kTuneMaxRestart, opts->krylov);
   if (s) return s;
   s = ensure_red(ctx);
   if (s) return s;

@@ -57,7 +57,7 @@ class jfnk_report(C.Structure):
                 ("krylov_its", C.c_int), ("jvp_calls", C.c_int), ("ls_backtracks", C.c_int),
                 ("ls_failures", C.c_int), ("krylov_failures", C.c_int), ("res0", C.c_double),
                 ("res_final", C.c_double), ("ms", C.c_double), ("dt_last", C.c_double),
-                ("ls_alpha", C.c_double * 16)]
+                ("ls_alpha", C.c_double * 16), ("restart_used", C.c_int)]
 
     def as_dict(self) -> dict:
         return {k: (list(getattr(self, k)) if k == "ls_alpha" else getattr(self, k)) for k, _ in self._fields_}
