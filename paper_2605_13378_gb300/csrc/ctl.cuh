@@ -37,6 +37,13 @@ struct GmresCtl {
   double da[kMaxM + 1];            // q_j = dgamma u_j - sum_i da[i] q_i
   double dc[kMaxM + 1];            // u_{j+1} = dinvr (w - sum_i dc[i] q_i - dc[j] q_j)
   double dgamma, dinvr;
+  // the inputs of the next step by step parity (step j reads slot j & 1): the
+  // deferred form runs step j in every block of the update pass while block 0
+  // writes its outputs, so what the step overwrites (hprev, g[j-1], its) is
+  // read from these copies
+  double hprev_p[2][kMaxM + 1];
+  double gprev_p[2];
+  int its_p[2];
 };
 constexpr size_t kGmresHeadBytes = 4 * sizeof(double) + 8 * sizeof(int) + sizeof(void*);
 
@@ -112,6 +119,8 @@ __device__ __forceinline__ void gmres_cycle_start(GmresCtl* c, double r2) {
     c->g[0] = beta;
     c->scale[0] = 1.0 / beta;
     c->active = 1;
+    c->gprev_p[0] = beta;
+    c->its_p[0] = c->its;
   }
   mirror_active(c->host_active, c->active);
 }
@@ -214,7 +223,9 @@ __device__ __forceinline__ void gmres_givens_step_block(GmresCtl* c, int j, doub
 }
 
 // Delayed CGS2 (the second Gram-Schmidt pass of each Arnoldi vector one step
-// late), step j, run by every thread of one block after the fused dots pass.
+// late), step j, run after the fused dots pass of step j: by its last block,
+// or (the deferred form) by every block of the update pass at its start, block
+// 0 alone writing the control state.
 // Slot j of the basis holds the candidate u_j (projected once, not
 // normalised); the JVP was applied to ut = sigma u_j, sigma = scale[j], giving
 // w. S holds the pass's sums: S[2i] = q_i . u_j, S[2i+1] = q_i . w for i < j,
@@ -257,13 +268,40 @@ __device__ __forceinline__ void dcgs_stage(GmresCtl* c, int j, double* sh, doubl
   }
 }
 
+// The threads that run a step together: a whole block (the dots pass's last
+// block, the fused pass), or the consumer warps 1.. of the update pass, which
+// run it while warp 0 keeps filling the ring (named barrier 1).
+struct BlockTeam {
+  __device__ int rank() const { return (int)threadIdx.x; }
+  __device__ int size() const { return (int)blockDim.x; }
+  __device__ void sync() const { __syncthreads(); }
+};
+struct ConsumerTeam {
+  __device__ int rank() const { return (int)threadIdx.x - 32; }
+  __device__ int size() const { return (int)blockDim.x - 32; }
+  __device__ void sync() const { asm volatile("bar.sync 1, %0;" ::"r"((int)blockDim.x - 32) : "memory"); }
+};
+
 // GB300 issues a warp's FP64 instruction over many cycles (two FP64 FMAs per
 // clock per SM), so each scalar is formed once, by one thread, and the
 // rotation chain carries one FMA per step; isig = 1 / sigma comes from the
 // caller, formed while the tail's loads are in flight.
-__device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
-                                          double sigma, double isig, double g_prev, double target, int m,
-                                          int active0, int its0) {
+//
+// kStagedH: the completed columns 0..j-2 are staged in `hs` (j (kMaxM + 1)
+// doubles; the new column j-1 is added there) and each row of z is one
+// sequential chain. Otherwise they are read from global memory, `hs` holds
+// only the new column (kMaxM + 1 doubles), and each row of z is split over
+// two or four threads of a warp with a fixed combining order.
+// Only the `writer` updates the control state (the rotation, H, Hraw, the
+// cycle's flags and the next step's inputs, also by step parity); every
+// caller gets the update pass's coefficients in o_da, o_dc, o_gamma, o_invr
+// (rounded to O: the control state's FP64, or the update pass's accumulator).
+// Returns whether the update pass of step j runs (every thread of the team).
+template <class Team, bool kStagedH, class O>
+__device__ __forceinline__ bool dcgs_step_t(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
+                                            double sigma, double isig, double g_prev, double target, int m,
+                                            int active0, int its0, Team tm, bool writer, O* o_da, O* o_dc,
+                                            O* o_gamma, O* o_invr) {
   constexpr int LD = kMaxM + 1;
   double* ss = sh;             // s
   double* zz = sh + LD;        // z
@@ -273,14 +311,16 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
   __shared__ int s_go, s_bad;
   __shared__ double s_s2, s_st, s_rho, s_irs, s_hn;
   __shared__ double s_cb[kMaxM + 1], s_sb[kMaxM + 1], s_a[kMaxM + 1];
-  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
-  const int cj = j - 1;
-  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+  const int r = tm.rank(), T = tm.size();
+  const int lane = r & 31, warp = r >> 5;
+  const int cj = j - 1, nxt = (j + 1) & 1;
+  double* hnew = kStagedH ? hs + (size_t)(j > 0 ? cj : 0) * LD : hs;   // the completed column j-1, unrotated
+  for (int i = r; i < j; i += T) {
     const double si = sigma * S[2 * i];
     ss[i] = si;
     col[i] += si * isig;
   }
-  __syncthreads();
+  tm.sync();
   if (warp == 0) {
     double v = 0.0;
     for (int i = lane; i < j; i += 32) v += ss[i] * ss[i];
@@ -292,9 +332,9 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
     v = warp_sum(v);
     if (lane == 0) s_st = v;
   }
-  __syncthreads();
-  // thread 0: rho (one rsqrt for rho and its reciprocal) and H[j, j-1]
-  if (threadIdx.x == 0) {
+  tm.sync();
+  // one thread: rho (one rsqrt for rho and its reciprocal) and H[j, j-1]
+  if (r == 0) {
     const double alpha = sigma * sigma * S[2 * j];
     const double rho2 = alpha - s_s2;
     const double irs = rho2 > 0.0 ? rsqrt(rho2) : 0.0;
@@ -303,24 +343,24 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
     s_hn = s_rho * isig;
     s_bad = !finite_d(rho2) || !finite_d(sigma);
   }
-  __syncthreads();
+  tm.sync();
   const double rho = s_rho, irs = s_irs, hn = s_hn;
   const bool bad = s_bad != 0;
-  // the completed (unrotated) column j-1 into hs, and the products of the
+  // the completed (unrotated) column j-1 into hnew, and the products of the
   // rotation chain that do not depend on the carried entry
   if (j > 0 && !bad) {
-    for (int i = threadIdx.x; i < j; i += blockDim.x) hs[(size_t)cj * LD + i] = col[i];
-    if (threadIdx.x == 0) {
-      hs[(size_t)cj * LD + j] = hn;
+    for (int i = r; i < j; i += T) hnew[i] = col[i];
+    if (r == 0) {
+      hnew[j] = hn;
       col[j] = hn;
     }
-    for (int i = threadIdx.x; i < cj; i += blockDim.x) {
+    for (int i = r; i < cj; i += T) {
       const double b = (i + 1 < j) ? col[i + 1] : hn;
       s_cb[i] = s_cs[i] * b;
       s_sb[i] = s_sn[i] * b;
     }
   }
-  __syncthreads();
+  tm.sync();
   if (warp == 0) {
     // rotation of column j-1, the residual estimate and the cycle's flags; the
     // other warps meanwhile form z, which needs only the unrotated columns
@@ -328,11 +368,16 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
       int active = active0;
       int go = 1;
       if (bad) {
-        c->nonfinite = 1;
+        if (writer) c->nonfinite = 1;
         active = 0;
         go = 0;
       } else if (j == 0) {
-        c->g[0] = g_prev * rho;      // r = beta rho q_0
+        const double g0 = g_prev * rho;   // r = beta rho q_0
+        if (writer) {
+          c->g[0] = g0;
+          c->gprev_p[nxt] = g0;
+          c->its_p[nxt] = its0;
+        }
       } else {
         // the carried entry a_{i+1} = -sn_i a_i + cs_i b_i: one dependent FMA per
         // rotation (the products cs_i b_i were formed above by all threads); the
@@ -346,22 +391,26 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
         const double r2 = fma(f, f, gg * gg);     // Hessenberg entries: no overflow in the squares
         double cs = 1.0, sn = 0.0;
         if (r2 != 0.0) { const double ir = rsqrt(r2); cs = f * ir; sn = gg * ir; }
-        c->cs[cj] = cs;
-        c->sn[cj] = sn;
         col[cj] = cs * f + sn * gg;
         col[cj + 1] = 0.0;
         const double g1 = -sn * g_prev;
-        c->g[cj + 1] = g1;
-        c->g[cj] = cs * g_prev;
-        c->k = j;
-        c->its = its0 + 1;                   // its0 staged with the other scalars: no load on this path
         const double res = fabs(g1);
-        c->resid = res;
+        if (writer) {
+          c->cs[cj] = cs;
+          c->sn[cj] = sn;
+          c->g[cj + 1] = g1;
+          c->g[cj] = cs * g_prev;
+          c->k = j;
+          c->its = its0 + 1;                 // its0 staged with the other scalars: no load on this path
+          c->resid = res;
+          c->gprev_p[nxt] = g1;
+          c->its_p[nxt] = its0 + 1;
+        }
         if (!finite_d(res) || !finite_d(hn)) {
-          c->nonfinite = 1;
+          if (writer) c->nonfinite = 1;
           active = 0;
         } else if (res <= target) {
-          c->converged = 1;
+          if (writer) c->converged = 1;
           active = 0;
         } else if (hn == 0.0 || j >= m) {   // lucky breakdown, or the end of the cycle
           active = 0;
@@ -373,47 +422,87 @@ __device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, b
         go = 0;
       }
       if (!has_w) go = 0;
-      if (!active) {
+      if (!active && writer) {
         c->active = 0;
         mirror_active(c->host_active, 0);
       }
       s_go = go;
     }
   } else if (!bad && has_w && rho != 0.0) {
-    // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg:
-    // one thread per row, a sequential FMA chain (few FP64 operations, so the
-    // rotation that warp 0 runs meanwhile keeps the FP64 pipe)
-    const int i = (int)threadIdx.x - 32;
-    if (i <= j) {
+    // z = H[:j+1, :j] s over the completed (unrotated) columns, upper Hessenberg
+    // (few FP64 operations, so the rotation that warp 0 runs meanwhile keeps the
+    // FP64 pipe)
+    if constexpr (kStagedH) {
+      // one thread per row, a sequential FMA chain
+      const int i = r - 32;
+      if (i <= j) {
+        double z = 0.0;
+        for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) z = fma(hs[(size_t)l * LD + i], ss[l], z);
+        zz[i] = z;
+      }
+    } else {
+      // P threads per row (the lanes of a row are adjacent in one warp), each
+      // taking every P-th completed column from global memory with eight loads in
+      // flight; the partial chains are combined by butterflies, then the newest
+      // column's term is added
+      const int P = (j + 1) * 4 <= T - 32 ? 4 : 2;
+      const int i = (r - 32) / P, q = (r - 32) - i * P;
       double z = 0.0;
-      for (int l = (i > 0 ? i - 1 : 0); l < j; ++l) z = fma(hs[(size_t)l * LD + i], ss[l], z);
-      zz[i] = z;
+      if (i <= j && j > 0) {
+        int l = (i > 0 ? i - 1 : 0) + q;
+        for (; l + 7 * P < cj; l += 8 * P) {
+          double h[8];
+#pragma unroll
+          for (int u = 0; u < 8; ++u) h[u] = __ldcg(&c->Hraw[(size_t)(l + u * P) * LD + i]);
+#pragma unroll
+          for (int u = 0; u < 8; ++u) z = fma(h[u], ss[l + u * P], z);
+        }
+        for (; l < cj; l += P) z = fma(__ldcg(&c->Hraw[(size_t)l * LD + i]), ss[l], z);
+      }
+      z += __shfl_xor_sync(0xffffffffu, z, 1);
+      if (P == 4) z += __shfl_xor_sync(0xffffffffu, z, 2);
+      if (q == 0 && i <= j) zz[i] = j > 0 ? fma(hnew[i], ss[cj], z) : 0.0;
     }
   }
-  __syncthreads();
+  tm.sync();
   // the completed column j-1 (unrotated and rotated) back to global memory;
   // rotated entries below the new rotation from the carried entries
-  if (j > 0 && !bad)
-    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
-      c->Hraw[(size_t)cj * LD + i] = hs[(size_t)cj * LD + i];
+  if (writer && j > 0 && !bad)
+    for (int i = r; i <= j; i += T) {
+      c->Hraw[(size_t)cj * LD + i] = hnew[i];
       c->H[(size_t)cj * LD + i] = i < cj ? fma(s_cs[i], s_a[i], s_sb[i]) : col[i];
     }
-  if (!s_go) return;
+  const bool go = s_go != 0;
+  if (!go) return false;
   const double irho = irs;
-  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+  for (int i = r; i < j; i += T) {
     const double h = (S[2 * i + 1] - zz[i]) * irho;
-    c->hprev[i] = h;
-    c->da[i] = ss[i] * irho;
-    c->dc[i] = zz[i] + rho * h;
+    if (writer) {
+      c->hprev[i] = h;
+      c->hprev_p[nxt][i] = h;
+    }
+    o_da[i] = (O)(ss[i] * irho);
+    o_dc[i] = (O)(zz[i] + rho * h);
   }
-  if (threadIdx.x == 0) {
+  if (r == 0) {
     const double qw = (sigma * S[2 * j + 1] - s_st) * irho;
     const double h = (qw - zz[j]) * irho;
-    c->hprev[j] = h;
-    c->dc[j] = zz[j] + rho * h;
-    c->dgamma = sigma * irho;
-    c->dinvr = irho;
+    if (writer) {
+      c->hprev[j] = h;
+      c->hprev_p[nxt][j] = h;
+    }
+    o_dc[j] = (O)(zz[j] + rho * h);
+    *o_gamma = (O)(sigma * irho);
+    *o_invr = (O)irho;
   }
+  return true;
+}
+
+__device__ __forceinline__ void dcgs_step(GmresCtl* c, int j, const double* S, bool has_w, double* sh, double* hs,
+                                          double sigma, double isig, double g_prev, double target, int m,
+                                          int active0, int its0) {
+  dcgs_step_t<BlockTeam, true, double>(c, j, S, has_w, sh, hs, sigma, isig, g_prev, target, m, active0, its0, BlockTeam{},
+                               true, c->da, c->dc, &c->dgamma, &c->dinvr);
 }
 
 // After the update pass of step j: q_j is stored normalised, u_{j+1} has

@@ -11,8 +11,10 @@
 // a shared-memory ring (bulk copies by producer warp 0, eight consumer warps);
 // the ring has as many entries as fit the device's per-block limit (227 KB on
 // GB300, less the kernel's static shared memory), so that short passes keep
-// more than one entry in flight while the consumers read another. Requires
-// n % 8 == 0, like the other streaming passes.
+// more than one entry in flight while the consumers read another. The update
+// pass takes each block's super-chunks in reverse order, so that it starts on
+// the chunks the dots pass read last, which the 129 MB L2 may still hold.
+// Requires n % 8 == 0, like the other streaming passes.
 #pragma once
 
 #include <type_traits>
@@ -38,10 +40,10 @@ static int dcgs_scb(int nv, bool has_w, int* stage) {
   return 0;
 }
 
-// producer: slots 0..nv-1 of super-chunk `it`, then (w not null) the w chunk,
-// into ring entry it % nst
+// producer: slots 0..nv-1 of this block's super-chunk `c`, then (w not null)
+// the w chunk, into ring entry it % nst (`it` counts the entries filled)
 template <class TB, class TJ>
-__device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, const TJ* w, int nv, int CE,
+__device__ __forceinline__ bool dcgs_produce(int it, int c, long long n, const TB* V, const TJ* w, int nv, int CE,
                                              int scb, int stage_bytes, int nst, unsigned char* sring, uint64_t* full,
                                              uint64_t* empty, unsigned int* err, int* s_abort) {
   const int lane = threadIdx.x & 31;
@@ -52,7 +54,7 @@ __device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, c
     return false;
   }
   if (*s_abort) return false;
-  const long long e0 = ((long long)blockIdx.x + (long long)it * gridDim.x) * CE;
+  const long long e0 = ((long long)blockIdx.x + (long long)c * gridDim.x) * CE;
   const long long rem = n - e0;
   const int cnt = rem < CE ? (int)rem : CE;
   const uint32_t vb = (uint32_t)cnt * sizeof(TB), wb = (uint32_t)cnt * sizeof(TJ);
@@ -75,11 +77,16 @@ __device__ __forceinline__ bool dcgs_produce(int it, long long n, const TB* V, c
 // Otherwise (FP64 accumulators, or longer bases, whose 2 KB chunks hold 128
 // slices) warps 1-4 accumulate q_i . u_j and warps 5-8 q_i . w, each of the
 // 128 threads of a group owning slices sl = t, t + 128, ...
-// The last block to finish sums the block partials and runs dcgs_step.
+// The last block to finish sums the block partials and runs dcgs_step; in the
+// deferred form (defer, with w) the pass ends when every block has stored its
+// partials, value-major after the first gridDim.x kMaxK doubles
+// (partials[G kMaxK + v G + b]), and every block of the update pass sums them
+// and runs the step itself.
 template <class TB, class TJ, int KMAX>
 __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     k_dcgs_dots(long long n, const TB* __restrict__ V, int j, const TJ* __restrict__ w, GmresCtl* ctl,
-                double* partials, unsigned int* counter, int cap, int scb, int stage_bytes, int nst, unsigned int* err) {
+                double* partials, unsigned int* counter, int cap, int scb, int stage_bytes, int nst, int defer,
+                unsigned int* err) {
   typedef typename AccS<TJ>::type A;
   constexpr int VW = 16 / (int)sizeof(TB);
   constexpr int NA = KMAX + 1;                 // accumulators: basis slots 0..j, j <= KMAX
@@ -88,7 +95,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   constexpr int NW = kJoint ? NA : 1;          // w accumulators of the joint form
   grid_dep_wait();      // the JVP that wrote w has completed (programmatic launch)
   grid_dep_trigger();
-  if (!ctl->active || (int)gridDim.x > cap) return;   // host sizing error: never write past the partials
+  const bool dfr = defer && w != nullptr;
+  // host sizing error: never write past the partials
+  if (!ctl->active || (dfr ? 2 : 1) * (int)gridDim.x > cap) return;
   extern __shared__ __align__(128) unsigned char sring[];
   uint64_t* full = (uint64_t*)(sring + (size_t)nst * stage_bytes);
   uint64_t* empty = full + nst;
@@ -119,7 +128,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   if (warp == 0) {
     int it = 0;
     for (; it < my; ++it)
-      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
+      if (!dcgs_produce<TB, TJ>(it, it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
     if (s_abort && lane == 0) {
       const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (it - nst > 0 ? it - nst : 0); q < it; ++q)
@@ -200,6 +209,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   // joint form, the four of each group in the split form); FP32 partials as
   // float-float pairs (the cross-block sums then stay in FP32 arithmetic)
   constexpr bool kFF = std::is_same<A, float>::value;
+  const int G = (int)gridDim.x;
+  double* const pdst = dfr ? partials + (size_t)G * kMaxK + blockIdx.x : partials + (size_t)blockIdx.x * kMaxK;
+  const int pstr = dfr ? G : 1;   // value stride of this block's partials
   if constexpr (kJoint) {
     __shared__ float redj[kStreamThreads / 32][2 * NA];
     if (warp >= 1) {
@@ -216,7 +228,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
       FF sum{redj[0][v], 0.0f};
 #pragma unroll
       for (int q = 1; q < kStreamThreads / 32; ++q) sum = ff_add(sum, FF{redj[q][v], 0.0f});
-      ff_store(&partials[(size_t)blockIdx.x * kMaxK + v], sum);
+      ff_store(&pdst[(size_t)v * pstr], sum);
     }
   } else {
     __shared__ double red[kStreamThreads / 32][NA];
@@ -236,15 +248,16 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
         FF sum{(float)red[4 * r][t], 0.0f};
 #pragma unroll
         for (int q = 1; q < 4; ++q) sum = ff_add(sum, FF{(float)red[4 * r + q][t], 0.0f});
-        ff_store(&partials[(size_t)blockIdx.x * kMaxK + v], sum);
+        ff_store(&pdst[(size_t)v * pstr], sum);
       } else {
         double sum = 0.0;
 #pragma unroll
         for (int q = 0; q < 4; ++q) sum += red[4 * r + q][t];
-        partials[(size_t)blockIdx.x * kMaxK + v] = sum;
+        pdst[(size_t)v * pstr] = sum;
       }
     }
   }
+  if (dfr) return;   // the update pass sums the partials (the kernel boundary orders them)
   __threadfence();
   __syncthreads();
   if (tid == 0) s_last = (atomicAdd(counter, 1u) == gridDim.x - 1);
@@ -259,7 +272,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   // one round of loads: every block's partials into the drained ring (when
   // they fit beside the completed Hessenberg columns), the control state into
   // shared memory
-  const int G = (int)gridDim.x, nval = 2 * nv;
+  const int nval = 2 * nv;
   const size_t ring = (size_t)nst * stage_bytes;
   // partials staged value-major with a padded row, [nval][G + 1], so that the
   // lanes of a warp summing one value read consecutive banks
@@ -415,22 +428,112 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   if (tid == 0) *counter = 0u;
 }
 
+// Start of the update pass in the deferred form, run by the consumer warps
+// while warp 0 fills the ring: the sums of the dots pass's block partials
+// (each value by one warp over the blocks in a fixed order, so that every
+// block forms the same bits), then dcgs_step_t with block 0 as the only
+// writer of the control state. The step's inputs that block 0 overwrites are
+// read from this step's parity slot; the completed Hessenberg columns are read
+// from global memory (no shared memory taken from the ring). The coefficients
+// go to ca, cc (cc[j] the coefficient of q_j), s_gamma, s_invr.
+template <class A>
+__device__ __forceinline__ bool dcgs_deferred_step(GmresCtl* ctl, int j, const double* __restrict__ dpart, int G,
+                                                   A* ca, A* cc, A* s_gamma, A* s_invr) {
+  constexpr int LD = kMaxM + 1;
+  constexpr bool kFF = std::is_same<A, float>::value;
+  __shared__ double S[2 * LD];
+  __shared__ double sh[5 * LD];
+  __shared__ double hcol[LD];
+  const ConsumerTeam tm;
+  const int r = tm.rank(), T = tm.size(), lane = r & 31, warp = r >> 5, nw = T >> 5;
+  const int nval = 2 * (j + 1), cj = j - 1, p = j & 1;
+  for (int i = r; i < j; i += T) {
+    sh[2 * LD + i] = __ldcg(&ctl->hprev_p[p][i]);
+    if (i < cj) { sh[3 * LD + i] = __ldcg(&ctl->cs[i]); sh[4 * LD + i] = __ldcg(&ctl->sn[i]); }
+  }
+  const double sigma = __ldcg(&ctl->scale[j]), g_prev = __ldcg(&ctl->gprev_p[p]), target = __ldcg(&ctl->target);
+  const int m = __ldcg(&ctl->m), its0 = __ldcg(&ctl->its_p[p]);
+  // four values per warp at once, five blocks per lane and value loaded ahead
+  // of the dependent adds (value-major partials: the lanes read adjacent words)
+  for (int v0 = warp; v0 < nval; v0 += 4 * nw) {
+    if constexpr (kFF) {
+      FF sum[4] = {{0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}, {0.0f, 0.0f}};
+      for (int b0 = lane; b0 < G; b0 += 5 * 32) {
+        FF x[4][5];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+#pragma unroll
+          for (int k = 0; k < 5; ++k) {
+            const int b = b0 + 32 * k;
+            x[u][k] = (v < nval && b < G) ? ff_load(&dpart[(size_t)v * G + b]) : FF{0.0f, 0.0f};
+          }
+        }
+#pragma unroll
+        for (int k = 0; k < 5; ++k) {
+#pragma unroll
+          for (int u = 0; u < 4; ++u)
+            if (b0 + 32 * k < G) sum[u] = ff_add(sum[u], x[u][k]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum[u] = warp_sum_ff(sum[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+          if (v < nval) S[v] = (double)sum[u].hi + (double)sum[u].lo;
+        }
+      }
+    } else {
+      double sum[4] = {0.0, 0.0, 0.0, 0.0};
+      for (int b = lane; b < G; b += 32) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+          if (v < nval) sum[u] += __ldcg(&dpart[(size_t)v * G + b]);
+        }
+      }
+#pragma unroll
+      for (int u = 0; u < 4; ++u) sum[u] = warp_sum(sum[u]);
+      if (lane == 0) {
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const int v = v0 + u * nw;
+          if (v < nval) S[v] = sum[u];
+        }
+      }
+    }
+  }
+  tm.sync();
+  // the pass runs only while the cycle is active (checked at its entry), so active0 = 1
+  return dcgs_step_t<ConsumerTeam, false, A>(ctl, j, S, true, sh, hcol, sigma, 1.0 / sigma, g_prev, target, m, 1,
+                                             its0, tm, blockIdx.x == 0, ca, cc, s_gamma, s_invr);
+}
+
+// Update pass. Deferred form (dpart, the dots pass's value-major partials):
+// warp 0 fills the free ring entries while the consumer warps run the step,
+// then both wait on named barrier 2 for its decision; when the step ends the
+// cycle the pass streams nothing (every block reaches the same decision) and
+// waits for its fills before it returns.
 template <class TB, class TJ, int KMAX>
 __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     k_dcgs_update(long long n, TB* __restrict__ V, int j, const TJ* __restrict__ w, GmresCtl* ctl,
-                  RedSite<typename AccS<TJ>::type> red, int scb, int stage_bytes, int nst, unsigned int* err) {
+                  RedSite<typename AccS<TJ>::type> red, const double* __restrict__ dpart, int scb, int stage_bytes,
+                  int nst, unsigned int* err) {
   typedef typename AccS<TJ>::type A;
   constexpr int VW = 16 / (int)sizeof(TB);
-  grid_dep_wait();      // the dots pass that formed the coefficients has completed
+  grid_dep_wait();      // the dots pass has completed
   grid_dep_trigger();
   if (!ctl->active) return;
   extern __shared__ __align__(128) unsigned char sring[];
   uint64_t* full = (uint64_t*)(sring + (size_t)nst * stage_bytes);
   uint64_t* empty = full + nst;
   __shared__ A ca[kMaxM + 1], cc[kMaxM + 1];
-  __shared__ A s_gamma, s_cj, s_invr;
-  __shared__ int s_abort;
+  __shared__ A s_gamma, s_invr;
+  __shared__ int s_abort, s_go;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const bool deferred = dpart != nullptr;
   if (tid == 0) {
     for (int q = 0; q < nst; ++q) {
       mbar_init(&full[q], 1);
@@ -438,14 +541,18 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     }
     fence_mbar_init();
     s_abort = 0;
-    s_gamma = (A)ctl->dgamma;
-    s_cj = (A)ctl->dc[j];
-    s_invr = (A)ctl->dinvr;
+    s_go = 1;
+    if (!deferred) {
+      s_gamma = (A)ctl->dgamma;
+      s_invr = (A)ctl->dinvr;
+      cc[j] = (A)ctl->dc[j];
+    }
   }
-  for (int t = tid; t < j; t += blockDim.x) {
-    ca[t] = (A)ctl->da[t];
-    cc[t] = (A)ctl->dc[t];
-  }
+  if (!deferred)
+    for (int t = tid; t < j; t += blockDim.x) {
+      ca[t] = (A)ctl->da[t];
+      cc[t] = (A)ctl->dc[t];
+    }
   __syncthreads();
   const int nv = j + 1;
   const int CE = scb / (int)sizeof(TB);
@@ -454,23 +561,39 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
   A acc[1] = {A(0)};
   if (warp == 0) {
     int it = 0;
-    for (; it < my; ++it)
-      if (!dcgs_produce<TB, TJ>(it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err, &s_abort)) break;
-    if (s_abort && lane == 0) {
+    const int pre = deferred ? (my < nst ? my : nst) : my;   // before the decision: the free entries only
+    for (; it < pre; ++it)
+      if (!dcgs_produce<TB, TJ>(it, my - 1 - it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty, err,
+                                &s_abort))
+        break;
+    if (deferred) {
+      named_sync(2, blockDim.x);   // the step's decision
+      if (s_go && !s_abort)
+        for (; it < my; ++it)
+          if (!dcgs_produce<TB, TJ>(it, my - 1 - it, n, V, w, nv, CE, scb, stage_bytes, nst, sring, full, empty,
+                                    err, &s_abort))
+            break;
+    }
+    if ((s_abort || !s_go) && lane == 0) {   // wait for the fills in flight before returning
       const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
       for (int q = (it - nst > 0 ? it - nst : 0); q < it; ++q)
         mbar_wait_until(&full[q % nst], (uint32_t)((q / nst) & 1), deadline);
     }
   } else {
-    const A gam = s_gamma, cj = s_cj, invr = s_invr;
-    for (int it = 0; it < my; ++it) {
+    if (deferred) {
+      const bool go = dcgs_deferred_step<A>(ctl, j, dpart, (int)gridDim.x, ca, cc, &s_gamma, &s_invr);
+      if (tid == 32) s_go = go;
+      named_sync(2, blockDim.x);
+    }
+    const A gam = s_gamma, cj = cc[j], invr = s_invr;
+    for (int it = 0; s_go && it < my; ++it) {
       const int sidx = it % nst;
       if (!mbar_wait_bounded(&full[sidx], (uint32_t)((it / nst) & 1), kWaitLimitNs)) {
         if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); s_abort = 1; }
         break;
       }
       if (s_abort) break;
-      const long long e0 = ((long long)blockIdx.x + (long long)it * gridDim.x) * CE;
+      const long long e0 = ((long long)blockIdx.x + (long long)(my - 1 - it) * gridDim.x) * CE;
       const long long rem = n - e0;
       const int cnt = rem < CE ? (int)rem : CE;
       const unsigned char* st = sring + (size_t)sidx * stage_bytes;
@@ -508,7 +631,7 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
     }
   }
   __syncthreads();
-  if (s_abort) return;
+  if (s_abort || !s_go) return;
   __shared__ A sm[9];
   __shared__ double s_n2;
   const bool last = grid_reduce<A, 1>(acc, 1, red, gridDim.x, blockIdx.x, sm, [&](int, A sv) { s_n2 = (double)sv; });
@@ -517,8 +640,9 @@ __global__ void __launch_bounds__(kStreamThreads + 32, 1)
 
 template <class TB, class TJ, int KMAX>
 static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                                 unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
+                                 unsigned int* err, int nsm, cudaStream_t st, bool pdl, bool defer) {
   typedef typename AccS<TJ>::type A;
+  if (defer && (w == nullptr || red.max_blocks < 2 * nsm)) return cudaErrorInvalidValue;
   int stage = 0;
   const int scb = dcgs_scb<TB, TJ>(j + 1, w != nullptr, &stage);
   if (scb == 0) return cudaErrorInvalidValue;
@@ -539,24 +663,27 @@ static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const vo
   if (pass == 1)
     e = launch_maybe_pdl(pdl, k_dcgs_dots<TB, TJ, KMAX>, dim3(nsm), dim3(kStreamThreads + 32), smem, st, n,
                          (const TB*)V, j, (const TJ*)w, ctl, (double*)red.partials, red.counter, red.max_blocks, scb,
-                         stage, nst, err);
+                         stage, nst, defer ? 1 : 0, err);
   else
     e = launch_maybe_pdl(pdl, k_dcgs_update<TB, TJ, KMAX>, dim3(nsm), dim3(kStreamThreads + 32), smem, st, n, (TB*)V,
-                         j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks}, scb, stage,
-                         nst, err);
+                         j, (const TJ*)w, ctl, RedSite<A>{(A*)red.partials, red.counter, red.max_blocks},
+                         defer ? (const double*)red.partials + (size_t)nsm * kMaxK : (const double*)nullptr, scb,
+                         stage, nst, err);
   if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
-// pass 1: dots of step j (w null: the last step of a cycle); pass 2: update of step j
+// pass 1: dots of step j (w null: the last step of a cycle); pass 2: update of step j.
+// defer (w not null, partials for at least 2 nsm blocks): the step runs at the start of
+// the update pass instead of the end of the dots pass; both passes of a step take the same value.
 template <class TB, class TJ>
 static cudaError_t dcgs_dispatch(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                                 unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
-  if (j < 8) return dcgs_launch_k<TB, TJ, 8>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
-  if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
-  if (j < 24) return dcgs_launch_k<TB, TJ, 24>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
-  if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
-  return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+                                 unsigned int* err, int nsm, cudaStream_t st, bool pdl, bool defer) {
+  if (j < 8) return dcgs_launch_k<TB, TJ, 8>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  if (j < 24) return dcgs_launch_k<TB, TJ, 24>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
 }
 
 }  // namespace jfnk

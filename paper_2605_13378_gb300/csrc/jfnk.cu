@@ -243,7 +243,8 @@ jfnk_status ensure_ws(jfnk_ctx* ctx, int prec, int m, int krylov) {
 
 jfnk_status ensure_red(jfnk_ctx* ctx) {
   int need = vec_blocks(ctx->N);
-  if (ctx->nsm > need) need = ctx->nsm;   // grid of the streaming kernels
+  if (2 * ctx->nsm > need) need = 2 * ctx->nsm;   // grid of the streaming kernels, and the deferred
+                                                  // delayed-CGS2 partials after its own kMaxK per block
   if (ctx->have_prob) {
     const StencilGeom g = stencil_geom(ctx->P);
     if (g.max_blocks > need) need = g.max_blocks;
@@ -418,12 +419,13 @@ struct Solver {
       if (s) return s;
       const double bs = (double)(j + 1) * nv * sb();
       int ev1 = tm_begin(ctx, KC_DCGS1, bs + nv * sj(), j);
+      // the coefficient step of step j runs at the start of its update pass (deferred form)
       cudaError_t e = launch_dcgs(1, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream,
-                                  pdl);
+                                  pdl, true);
       tm_end(ctx, ev1);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs dots kernel");
       int ev2 = tm_begin(ctx, KC_DCGS2, bs + nv * sj() + 2.0 * nv * sb(), j + 1);   // did work iff j < k
-      e = launch_dcgs(2, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream, pdl);
+      e = launch_dcgs(2, tb, tj, N, w.V, j, w.w, ctx->gctl, ctx->red, ctx->derr, ctx->nsm, ctx->stream, pdl, true);
       tm_end(ctx, ev2);
       if (e != cudaSuccess) return cuda_fail(ctx, e, "dcgs update kernel");
       if (!pdl) CK(cudaEventRecord(ctx->iter_ev[j % (kLookahead + 1)], ctx->stream), "event record");

@@ -155,11 +155,11 @@ cudaError_t launch_basis_stream(int mode, int tb, int tj, int td, long long n, c
 }
 
 cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, const void* w, GmresCtl* ctl,
-                        RedWs red, unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
+                        RedWs red, unsigned int* err, int nsm, cudaStream_t st, bool pdl, bool defer) {
   if (!stream_supported(n) || j < 0 || j > kMaxM || (pass != 1 && pass != 2)) return cudaErrorInvalidValue;
-  if (tb == VT_F64 && tj == VT_F64) return dcgs_f64(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
-  if (tb == VT_F32 && tj == VT_F32) return dcgs_f32(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
-  if (tb == VT_BF16 && tj == VT_F32) return dcgs_bf16(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+  if (tb == VT_F64 && tj == VT_F64) return dcgs_f64(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  if (tb == VT_F32 && tj == VT_F32) return dcgs_f32(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  if (tb == VT_BF16 && tj == VT_F32) return dcgs_bf16(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
   return cudaErrorInvalidValue;
 }
 

@@ -40,13 +40,16 @@ cudaError_t launch_basis_stream(int mode, int tb, int tj, int td, long long n, c
 // Delayed CGS2 (dcgs_impl.cuh, ctl.cuh dcgs_step): pass 1 the fused dots of
 // Arnoldi step j over basis slots 0..j and w (w null: the last step of a
 // cycle, which only completes column j - 1), pass 2 the fused update of step
-// j. Requires stream_supported(n).
+// j. Requires stream_supported(n). defer: the coefficient step of step j runs at
+// the start of its update pass, in every block, instead of at the end of its
+// dots pass (w not null; the partials must hold 2 nsm blocks); both passes of
+// the step take the same value.
 cudaError_t dcgs_f64(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                     unsigned int* err, int nsm, cudaStream_t st, bool pdl = false);
+                     unsigned int* err, int nsm, cudaStream_t st, bool pdl = false, bool defer = false);
 cudaError_t dcgs_f32(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                     unsigned int* err, int nsm, cudaStream_t st, bool pdl = false);
+                     unsigned int* err, int nsm, cudaStream_t st, bool pdl = false, bool defer = false);
 cudaError_t dcgs_bf16(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                      unsigned int* err, int nsm, cudaStream_t st, bool pdl = false);
+                      unsigned int* err, int nsm, cudaStream_t st, bool pdl = false, bool defer = false);
 // Fused delayed-CGS2 Arnoldi pass for the AD JVP, FP32 basis and JVP, 2D
 // PDEs with face neighbours only (Allen-Cahn, Maxwell TE, 2D Burgers):
 // q_j -> basis slot j, u_{j+1} = U_out, J u_{j+1} -> W_out (when has_w), and
@@ -61,7 +64,7 @@ cudaError_t launch_dcgs_fused(const ProbDev& P, long long n, void* V, int j, boo
 
 // pdl: launched programmatically after the kernel before it (see grid_dep_wait in stream.cuh)
 cudaError_t launch_dcgs(int pass, int tb, int tj, long long n, void* V, int j, const void* w, GmresCtl* ctl,
-                        RedWs red, unsigned int* err, int nsm, cudaStream_t st, bool pdl = false);
+                        RedWs red, unsigned int* err, int nsm, cudaStream_t st, bool pdl = false, bool defer = false);
 cudaError_t launch_cast(int ti, int to, long long n, const void* x, void* y, double c, cudaStream_t st);
 // Reset the line-search control of one Newton step (LsCtl): merit fnorm, trial alpha = 1.
 cudaError_t launch_ls_begin(LsCtl* c, double fnorm, double c1, double min_alpha, int accept_first, cudaStream_t st);

@@ -12,8 +12,8 @@ cudaError_t basis_stream_bf16(int mode, long long n, const void* V, int k, int k
 }
 
 cudaError_t dcgs_bf16(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                     unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
-  return dcgs_dispatch<__nv_bfloat16, float>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+                     unsigned int* err, int nsm, cudaStream_t st, bool pdl, bool defer) {
+  return dcgs_dispatch<__nv_bfloat16, float>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
 }
 
 }  // namespace jfnk

@@ -13,8 +13,8 @@ cudaError_t basis_stream_f32(int mode, int td, long long n, const void* V, int k
 }
 
 cudaError_t dcgs_f32(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                     unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
-  return dcgs_dispatch<float, float>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+                     unsigned int* err, int nsm, cudaStream_t st, bool pdl, bool defer) {
+  return dcgs_dispatch<float, float>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
 }
 
 }  // namespace jfnk

@@ -12,8 +12,8 @@ cudaError_t basis_stream_f64(int mode, long long n, const void* V, int k, int km
 }
 
 cudaError_t dcgs_f64(int pass, long long n, void* V, int j, const void* w, GmresCtl* ctl, RedWs red,
-                     unsigned int* err, int nsm, cudaStream_t st, bool pdl) {
-  return dcgs_dispatch<double, double>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl);
+                     unsigned int* err, int nsm, cudaStream_t st, bool pdl, bool defer) {
+  return dcgs_dispatch<double, double>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
 }
 
 }  // namespace jfnk
