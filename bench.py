@@ -343,10 +343,11 @@ def served_stream(J, device: int, n_req: int) -> dict:
         o.restart, o.max_newton, o.max_krylov = m, max_newton, max_cycles
         o.tol_newton = 1e-10
         o.tol_krylov = 1e-6 if prec == J.JFNK_MIXED_FP32 else 1e-10
-        # large mixed requests run on the slot workers, where delayed CGS2 streams the basis faster; the
-        # batch engine takes the others (CGS2)
+        # mixed requests use delayed CGS2: in the batch engine (small requests, any size) and on the slot
+        # workers (large ones, whose streaming passes need a size divisible by 8); FP64 requests the plain CGS2
         big = x0.size > (1 << 20)
-        o.ortho = J.JFNK_DCGS2 if (big and prec == J.JFNK_MIXED_FP32 and x0.size % 8 == 0) else J.JFNK_CGS2
+        dc = prec == J.JFNK_MIXED_FP32 and (not big or x0.size % 8 == 0)
+        o.ortho = J.JFNK_DCGS2 if dc else J.JFNK_CGS2
         return p, o, x0
 
     solves = lambda r: 1 if r["pde"] == "maxwell" else r["steps"]
@@ -373,12 +374,18 @@ def served_stream(J, device: int, n_req: int) -> dict:
                 rep = J.jfnk_report()
                 s = J.jfnk_poll(ctx, t, rep)
                 if s != J.JFNK_E_BUSY:
-                    served[i] = (s, rep.ms, s == J.JFNK_OK and rep.steps_failed == 0)
+                    served[i] = (s, rep.ms, s == J.JFNK_OK and rep.steps_failed == 0, time.perf_counter() - t0)
                     del pending[i]
             time.sleep(0.0005)
         wall = time.perf_counter() - t0
     finally:
         J.jfnk_destroy(ctx)
+    # requests that ended in an error (not a missed tolerance): index, class, grid, status, completion time
+    errors = [{"request": i, "pde": reqs[i]["pde"], "n": reqs[i]["n"], "precision": reqs[i]["precision"],
+               "status": J.jfnk_status_string(served[i][0]), "t_done_s": round(served[i][3], 3)}
+              for i in sorted(served) if served[i][0] not in (J.JFNK_OK, J.JFNK_E_NOT_CONVERGED)]
+    if errors:
+        return {"requests": len(reqs), "error": "served requests failed", "failed": errors}
     # the same requests, one at a time, plain FP64
     c1 = J.jfnk_create(device)
     x64, ok64 = [], []
@@ -849,7 +856,12 @@ def main() -> None:
 
     cpu = cpu_baseline(a.cpu_sample_iters) if (rank == 0 and world == 1 and not a.no_cpu) else None
     J.jfnk_destroy(ctx)
-    served = None if a.no_serve else served_stream(J, local, a.serve_requests)
+    served = None
+    if not a.no_serve:
+        try:
+            served = served_stream(J, local, a.serve_requests)
+        except Exception as e:   # reported in the line; the measurements above stand
+            served = {"error": f"{type(e).__name__}: {e}"}
     if rank != 0:
         return
     out = {
@@ -869,7 +881,7 @@ def main() -> None:
         "timed_with_kernel_events_ms_per_step": sum(ms_t) / a.steps,
         "e2e": e2e, "cpu_baseline": cpu, "clocks": clk, "served": served,
     }
-    if served:
+    if served and "error" not in served:
         f = served["fp64_one_by_one"]
         out["served_fp32_vs_fp64"] = {
             "served_solves_per_s": served["value"], "fp64_one_by_one_solves_per_s": f["value"],

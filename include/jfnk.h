@@ -125,7 +125,8 @@ typedef enum { JFNK_PRECOND_NONE = 0, JFNK_PRECOND_CSLP = 1 } jfnk_precond;
  * pass over the basis. Same Krylov space, basis and iterates in exact
  * arithmetic; each cycle that converges before its last column applies the
  * Jacobian once more. DCGS2 runs on the streaming kernels: N (all fields) a
- * multiple of 8, else JFNK_E_INVALID. The batched entry points use CGS2. */
+ * multiple of 8, else JFNK_E_INVALID. The batched entry points take CGS2 or
+ * DCGS2 (any N: there the passes are phases of the batch kernel). */
 /* JFNK_DCGS2_FUSED is delayed CGS2 with the update of step j, the AD JVP of
  * the next candidate and the dots of step j + 1 in one kernel, so the basis
  * is read once per step instead of twice. It needs lin = JFNK_AD, prec =
@@ -248,12 +249,12 @@ jfnk_status jfnk_solve(jfnk_ctx* ctx, const jfnk_opts* opts, const double* x_pre
 /* Batched solves: `count` independent problems solved together, each with
  * its own options (probs[i], opts[i]) and step count (steps[i]; ignored for
  * the Maxwell problem), each exactly as jfnk_solve would define it (Newton
- * with the Armijo line search of Sec. 2, restarted GMRES with CGS2 Arnoldi
- * of Sec. 3, the AD JVP of Eq. 9 or the FD quotient of Eq. 7, the theta
+ * with the Armijo line search of Sec. 2, restarted GMRES with CGS2 or delayed
+ * CGS2 Arnoldi of Sec. 3 (opts[i].ortho; JFNK_DCGS2_FUSED is refused), the AD JVP of Eq. 9 or the FD quotient of Eq. 7, the theta
  * method of Eq. 2, the Born start). The state of every solve lives on the
  * device; each launch of the batch kernel advances every unfinished solve by
- * one phase of that iteration (a JVP sweep, one Gram-Schmidt pass, a
- * residual, a line-search trial ...), and the host replays a captured CUDA
+ * one phase of that iteration (a JVP sweep, one Gram-Schmidt pass or the
+ * delayed form's dots or update pass, a residual, a line-search trial ...), and the host replays a captured CUDA
  * graph of such launches until all are done, so small solves share launches
  * instead of each paying its own launch and synchronisation latency.
  * Supported: krylov = JFNK_GMRES, prec = JFNK_FP64, JFNK_FP32 or

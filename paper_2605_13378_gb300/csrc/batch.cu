@@ -129,7 +129,10 @@ bool BatchEngine::supports(const jfnk_problem* pr, const jfnk_opts* o, std::stri
   if (!(o->tol_newton >= 0) || !(o->tol_krylov >= 0)) { if (why) *why = "bad tolerances"; return false; }
   if (!(o->ls_min_alpha > 0.0 && o->ls_min_alpha <= 1.0)) { if (why) *why = "bad ls_min_alpha"; return false; }
   if (o->fd_rule != JFNK_EPS_SCALED && o->fd_rule != JFNK_EPS_PAPER) { if (why) *why = "bad fd_rule"; return false; }
-  if (o->ortho != JFNK_CGS2) { if (why) *why = "batched solves use CGS2 Arnoldi"; return false; }
+  if (o->ortho != JFNK_CGS2 && o->ortho != JFNK_DCGS2) {
+    if (why) *why = "batched solves use CGS2 or delayed CGS2 Arnoldi";
+    return false;
+  }
   if (pr->pde == JFNK_MAXWELL_VEC2D || o->precond != JFNK_PRECOND_NONE) {
     if (why) *why = "the vector Maxwell problem and its preconditioner run through jfnk_solve";
     return false;
@@ -244,6 +247,7 @@ jfnk_status BatchEngine::admit(const BatRequest& r, std::string* why) {
   D.max_newton = r.opts.max_newton; D.max_krylov = r.opts.max_krylov;
   D.steps = P.bvp ? 1 : r.steps;
   D.born = (P.bvp && r.opts.born_start) ? 1 : 0;
+  D.ortho = r.opts.ortho;
   D.tol_newton = r.opts.tol_newton; D.tol_krylov = r.opts.tol_krylov;
   D.fd_eps = r.opts.fd_eps; D.ls_c1 = r.opts.ls_c1; D.ls_min_alpha = r.opts.ls_min_alpha;
   D.done_flag = d_flags_ + slot;

@@ -21,7 +21,7 @@ namespace jfnk {
 
 constexpr int kBatThreads = 256;   // threads per CTA
 constexpr int kBatUnit = 256;      // cells per reduction unit
-constexpr int kBatPart = 72;       // partial sums kept per unit (>= kMaxM + 1)
+constexpr int kBatPart = 136;      // partial sums kept per unit (>= 2 (kMaxM + 1): delayed-CGS2 dots)
 
 enum BatPhase {
   PH_IN = 0,     // state <- caller's initial value (zero for the Born stage)
@@ -37,6 +37,8 @@ enum BatPhase {
   PH_GUPD,       // d += V y
   PH_RJVP,       // restart: u_0 = rhs - J d, ||u_0||^2
   PH_LS,         // trial x + alpha d: F, ||F||^2, ||x + alpha d||^2 -> Armijo test
+  PH_D1,         // delayed CGS2: q_i . u_j, q_i . w (i <= j) -> the coefficient step (whole CTA)
+  PH_D2,         // delayed CGS2: q_j -> slot j, u_{j+1} -> slot j + 1, ||u_{j+1}||^2
   PH_OUT,        // caller's result <- state
   PH_DONE
 };
@@ -59,6 +61,7 @@ struct BatDesc {
   int tc, ntile, nunit;            // cells per tile, tiles, reduction units
   int ts, tj;                      // state and JVP / basis precision (VT_F64, VT_F32)
   int lin, fd_rule, m, max_newton, max_krylov, steps, born;
+  int ortho;                       // JFNK_CGS2 (phases A1-A3) or JFNK_DCGS2 (phases D1-D2)
   double tol_newton, tol_krylov, fd_eps, ls_c1, ls_min_alpha;
   void* x[2]; void* F[2]; float* x32[2];
   void* b; float* b32; float* F32;

@@ -399,6 +399,87 @@ struct BatTile {
     }
   }
 
+  // Delayed CGS2, dots of step j (Sec. 3; the single-solve form is dcgs_step in
+  // ctl.cuh): per unit, q_i . u_j and q_i . w for i <= j (slot j holds the
+  // candidate u_j), warp per (unit, i); without w (the last step of a cycle,
+  // j = m) the w entries are zero.
+  __device__ static void dcgs_dots(const BatDesc& D, const BatState& S, int t) {
+    const long long nc = D.P.ncell, N = D.N;
+    const int j = S.j, k = j + 1;
+    const bool has_w = j < S.g.m;
+    const TJ* V = (const TJ*)D.V;
+    const TJ* uj = V + (long long)j * N;
+    const TJ* w = (const TJ*)D.w;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+    const long long ub0 = (long long)t * (D.tc / kBatUnit);
+    const long long ub1 = min(ub0 + D.tc / kBatUnit, (long long)D.nunit);
+    const int pairs = (int)(ub1 - ub0) * k;
+    for (int p = warp; p < pairs; p += nw) {
+      const long long ub = ub0 + p / k;
+      const int i = p % k;
+      const long long cu0 = ub * kBatUnit, cu1 = min(cu0 + kBatUnit, nc);
+      const TJ* qi = V + (long long)i * N;
+      A au = A(0), aw = A(0);
+#pragma unroll
+      for (int f = 0; f < NF; ++f)
+        for (long long c = cu0 + lane; c < cu1; c += 32) {
+          const long long g = f * nc + c;
+          const A q = (A)qi[g];
+          au += q * (A)uj[g];
+          if (has_w) aw += q * (A)w[g];
+        }
+      au = warp_sum(au);
+      aw = warp_sum(aw);
+      if (lane == 0) {
+        D.part[ub * kBatPart + 2 * i] = (double)au;
+        D.part[ub * kBatPart + 2 * i + 1] = (double)aw;
+      }
+    }
+  }
+
+  // Delayed CGS2, update of step j from the step's coefficients:
+  // q_j = dgamma u_j - sum_i da_i q_i (over slot j), u_{j+1} = dinvr (w -
+  // sum_i dc_i q_i - dc_j q_j) (slot j + 1), ||u_{j+1}||^2 per unit.
+  __device__ static void dcgs_update(const BatDesc& D, const BatState& S, int t) {
+    __shared__ A ca[kMaxM + 1], cc[kMaxM + 1], s_gi[2];
+    const long long nc = D.P.ncell, N = D.N;
+    const int j = S.j;
+    for (int i = threadIdx.x; i <= j; i += blockDim.x) {
+      ca[i] = (A)S.g.da[i];
+      cc[i] = (A)S.g.dc[i];
+    }
+    if (threadIdx.x == 0) { s_gi[0] = (A)S.g.dgamma; s_gi[1] = (A)S.g.dinvr; }
+    __syncthreads();
+    const A gam = s_gi[0], invr = s_gi[1], cj = cc[j];
+    TJ* V = (TJ*)D.V;
+    const TJ* w = (const TJ*)D.w;
+    const long long ub0 = (long long)t * (D.tc / kBatUnit);
+    const long long ub1 = min(ub0 + D.tc / kBatUnit, (long long)D.nunit);
+    for (long long ub = ub0; ub < ub1; ++ub) {
+      const long long c = ub * kBatUnit + threadIdx.x;
+      double acc[1] = {0.0};
+      if (c < nc) {
+#pragma unroll
+        for (int f = 0; f < NF; ++f) {
+          const long long g = f * nc + c;
+          A q = gam * (A)V[(long long)j * N + g];
+          A y = (A)w[g];
+          for (int i = 0; i < j; ++i) {
+            const A v = (A)V[(long long)i * N + g];
+            q -= ca[i] * v;
+            y -= cc[i] * v;
+          }
+          const TJ qs = (TJ)q;
+          const TJ ys = (TJ)((y - cj * (A)qs) * invr);
+          V[(long long)j * N + g] = qs;
+          V[(long long)(j + 1) * N + g] = ys;
+          acc[0] += (double)ys * (double)ys;
+        }
+      }
+      bat_unit_sum<1>(acc, D.part + ub * kBatPart);
+    }
+  }
+
   // per unit: max|u|, max|v| of the state (a non-finite value counts as +Inf)
   __device__ static void cfl_max(const BatDesc& D, const ProbDev& P, const BatState& S, int t) {
     const long long nc = P.ncell;
@@ -461,6 +542,8 @@ struct BatTile {
       case PH_A1: arnoldi(D, S, t, 1, ws); break;
       case PH_A2: arnoldi(D, S, t, 2, ws); break;
       case PH_A3: arnoldi(D, S, t, 3, ws); break;
+      case PH_D1: dcgs_dots(D, S, t); break;
+      case PH_D2: dcgs_update(D, S, t); break;
       case PH_GUPD: update(D, S, t); break;
       case PH_OUT: {
         const TS* x = (const TS*)D.x[S.cur];
@@ -552,7 +635,7 @@ __device__ __forceinline__ void bat_cycle_end(const BatDesc& D, BatState& S) {
   S.phase = PH_GUPD;
 }
 
-__device__ __forceinline__ void bat_control(const BatDesc& D, BatState& S, int ph, const double* sum) {
+__device__ __forceinline__ void bat_control(const BatDesc& D, BatState& S, int ph, const double* sum, bool go) {
   GmresCtl& g = S.g;
   if (S.stage == 2) {   // tile-size probe: the four phases of an Arnoldi step in a loop, fixed j
     S.phase = (ph == PH_A3) ? PH_JVP : ph + 1;
@@ -610,7 +693,19 @@ __device__ __forceinline__ void bat_control(const BatDesc& D, BatState& S, int p
       break;
     case PH_JVP:
       S.jvp_calls += 1;
-      S.phase = PH_A1;
+      S.phase = D.ortho == JFNK_DCGS2 ? PH_D1 : PH_A1;
+      break;
+    case PH_D1:   // the coefficient step ran on the whole CTA (k_batch); go: the update pass follows
+      if (go) S.phase = PH_D2; else bat_cycle_end(D, S);
+      break;
+    case PH_D2:
+      dcgs_after_update(&g, S.j, sum[0]);
+      if (g.nonfinite) {
+        bat_after_cycle(D, S);
+      } else {
+        S.j += 1;   // the next step, or (j = m) the last dots pass of the cycle, which has no w
+        S.phase = S.j < g.m ? PH_JVP : PH_D1;
+      }
       break;
     case PH_A1:
       for (int i = 0; i <= S.j; ++i) g.h1[i] = sum[i] * g.scale[i];
@@ -670,9 +765,31 @@ __device__ __forceinline__ int bat_nvals(const BatState& S, int ph) {
   switch (ph) {
     case PH_RES: case PH_LS: case PH_CFL: return 2;
     case PH_A1: case PH_A2: return S.j + 1;
-    case PH_A3: case PH_GUPD: case PH_RJVP: return 1;
+    case PH_D1: return 2 * (S.j + 1);
+    case PH_A3: case PH_GUPD: case PH_RJVP: case PH_D2: return 1;
     default: return 0;
   }
+}
+
+// The delayed-CGS2 coefficient step of a solve (dcgs_step_t, ctl.cuh) on the
+// CTA that finished its dots pass, from the unit sums S: the scalars and the
+// previous column's first projection and rotations are staged in shared
+// memory, the completed Hessenberg columns are read from the solve's state.
+__device__ __forceinline__ bool bat_dcgs_step(BatState& S, const double* sum) {
+  constexpr int LD = kMaxM + 1;
+  __shared__ double sh[5 * LD];
+  __shared__ double hcol[LD];
+  GmresCtl& g = S.g;
+  const int j = S.j, cj = j - 1;
+  for (int i = threadIdx.x; i < j; i += blockDim.x) {
+    sh[2 * LD + i] = g.hprev[i];
+    if (i < cj) { sh[3 * LD + i] = g.cs[i]; sh[4 * LD + i] = g.sn[i]; }
+  }
+  const double sigma = g.scale[j], g_prev = j > 0 ? g.g[j - 1] : g.g[0], target = g.target;
+  const int m = g.m, active = g.active, its = g.its;
+  __syncthreads();
+  return dcgs_step_t<BlockTeam, false, double>(&g, j, sum, j < m, sh, hcol, sigma, 1.0 / sigma, g_prev, target, m,
+                                               active, its, BlockTeam{}, true, g.da, g.dc, &g.dgamma, &g.dinvr);
 }
 
 // ---------------------------------------------------------------------------
@@ -719,9 +836,11 @@ __global__ void __launch_bounds__(kBatThreads) k_batch(BatLaunch L) {
           if (lane == 0) s_sum[v] = s;
         }
         __syncthreads();
+        bool go = false;
+        if (ph == PH_D1 && S.stage != 2) go = bat_dcgs_step(S, s_sum);   // every thread of the CTA
         if (threadIdx.x == 0) {
           S.arrive = 0u;
-          bat_control(D, S, ph, s_sum);
+          bat_control(D, S, ph, s_sum, go);
           __threadfence();
         }
       }

@@ -654,8 +654,14 @@ static cudaError_t stencil_launch(const ProbDev& P, const StencilArgs& a, RedWs 
           StagePlan sp;
           if (a.err && P.nx >= kStageWarps * 32 * VEC && P.ny >= 64 && aligned(a.v, 16) &&
               stage_plan<T, TV, PDE::NF>(P, num_sms(), &sp)) {
+            // opt in once at the per-block limit, so that every later plan (another grid) fits
+            static SmemLimit limit_of;
             static SmemOptIn opt_in;
-            cudaError_t e = smem_opt_in(k_jvp_stage<PDE, T, TV, MODE>, opt_in, sp.smem);
+            int limit = 0;
+            cudaError_t e = smem_block_limit(k_jvp_stage<PDE, T, TV, MODE>, limit_of, &limit);
+            if (e != cudaSuccess) return e;
+            if (sp.smem > limit) return cudaErrorInvalidValue;
+            e = smem_opt_in(k_jvp_stage<PDE, T, TV, MODE>, opt_in, limit);
             if (e != cudaSuccess) return e;
             e = launch_maybe_pdl(a.pdl != 0, k_jvp_stage<PDE, T, TV, MODE>, dim3(sp.grid), dim3(kStageThreads),
                                  (size_t)sp.smem, st, P, a, sp);
