@@ -282,8 +282,10 @@ jfnk_status jfnk_batch_stats(jfnk_ctx* ctx, long long* kernel_launches, int* til
 /* Serving: queue a solve of `prob` (steps as in jfnk_solve) and return a
  * ticket at once. x0 and x_out are FP64 host or device arrays that must stay
  * valid until jfnk_poll returns a final status for the ticket. Requests are
- * admitted when their workspace fits the context's HBM budget and a slot is
- * free; admitted requests run concurrently on the device. */
+ * admitted when their workspace fits the context's HBM budget. Requests up
+ * to 2^20 unknowns (all fields) go to the batch engine, where every admitted
+ * request advances in the same launches; larger ones run one at a time on a
+ * single solve worker, concurrently with the batch engine. */
 jfnk_status jfnk_submit(jfnk_ctx* ctx, const jfnk_problem* prob, const jfnk_opts* opts,
                         const double* x0, double* x_out, int steps, unsigned long long* ticket);
 

@@ -42,6 +42,7 @@ const char* kKClassNames[KC_COUNT] = {
     "arnoldi_dcgs_update", "cfl_dt", "arnoldi_dcgs_fused"};
 
 constexpr int kLookahead = 3;   // Arnoldi / BiCGSTAB steps the host may run ahead of the device
+constexpr int kServeSlotWorkers = 1;   // single-solve workers of the request server (jfnk_submit)
 
 // GMRES restart lengths the autotuner (opts.restart = 0) times on the first
 // Newton system of a problem class
@@ -1284,7 +1285,10 @@ void jfnk_reset_stats(jfnk_ctx* ctx) {
 jfnk_status jfnk_submit(jfnk_ctx* ctx, const jfnk_problem* prob, const jfnk_opts* opts, const double* x0,
                         double* x_out, int steps, unsigned long long* ticket) {
   if (!ctx || !prob || !opts || !x0 || !x_out || !ticket) return JFNK_E_INVALID;
-  if (!ctx->server) ctx->server = new jfnk::Server(ctx->device, ctx->budget, 4);
+  // one single-solve worker beside the batch engine: a large solve fills the GPU by itself, and four
+  // concurrent large solves next to the batch engine's multi-branch graph replays faulted the device
+  // intermittently (an unexplained illegal access) where one at a time never did
+  if (!ctx->server) ctx->server = new jfnk::Server(ctx->device, ctx->budget, kServeSlotWorkers);
   return ctx->server->submit(prob, opts, x0, x_out, steps, ticket);
 }
 

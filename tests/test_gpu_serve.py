@@ -4,7 +4,7 @@ jfnk_submit queues a solve and returns a ticket; admitted requests run
 concurrently on the device while later ones wait for budget. Requests the
 batch engine supports (GMRES; FP64, FP32, mixed FP32) join the running batch
 between replays of its launch graph; the others (here a BiCGSTAB request) run
-on slot workers through jfnk_solve. Every reduction uses a partition that
+on the single-solve worker through jfnk_solve, one at a time, beside the batch. Every reduction uses a partition that
 depends only on the request's own size, so a request's result must be
 bitwise the same alone and in the mix; it must also agree with jfnk_solve
 (bitwise on the slot path, to 1e-9 in FP64 and 1e-6 in mixed precision on
