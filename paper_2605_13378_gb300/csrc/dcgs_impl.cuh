@@ -683,6 +683,10 @@ static cudaError_t dcgs_dispatch(int pass, long long n, void* V, int j, const vo
   if (j < 16) return dcgs_launch_k<TB, TJ, 16>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
   if (j < 24) return dcgs_launch_k<TB, TJ, 24>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
   if (j < 32) return dcgs_launch_k<TB, TJ, 32>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  // buckets of eight up to 48: the slot loops are unrolled to KMAX, so a wide bucket spends issue
+  // slots on predicated-off slots (and registers on their accumulators)
+  if (j < 40) return dcgs_launch_k<TB, TJ, 40>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
+  if (j < 48) return dcgs_launch_k<TB, TJ, 48>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
   return dcgs_launch_k<TB, TJ, 64>(pass, n, V, j, w, ctl, red, err, nsm, st, pdl, defer);
 }
 
