@@ -162,8 +162,8 @@ typedef struct {
                          m = 10, 20, 30, 40, 60 to tol_krylov, times them, keeps the fastest
                          that converged for that class on the context and uses its step (so
                          the choice is made at equal tolerance, not equal iterates). Only
-                         jfnk_solve and the served slot workers; the batched entry points
-                         need m >= 1. */
+                         jfnk_solve and the server's single-solve worker; the batched entry
+                         points need m >= 1. */
   int max_newton;     /* Newton iterations per nonlinear solve */
   int max_krylov;     /* GMRES restart cycles; BiCGSTAB / CG iterations */
   double tol_newton;  /* Eq. 5 */
