@@ -172,7 +172,7 @@ def maxwell_vec_source(nx: int, ny: int | None = None, kind: str = "gauss", sigm
     (x_i = i/(nx - 1)): planes [Re Jx, Im Jx, Re Jy, Im Jy] with J_y = 0 and a real J_x,
       gauss:  J_x = exp(-((x - x0)^2 + (y - y0)^2) / (2 sigma^2)),
       dipole: J_x = exp(-((x - x0)^2 + (y - y1)^2) / (2 sigma^2)) - exp(-((x - x0)^2 + (y - y2)^2) / (2 sigma^2)),
-    y1, y2 = y0 -+ sep. The paper does not give x0, the y's or sigma; these defaults are this build's reading."""
+    y1, y2 = y0 -+ sep. The paper does not give x0, the y's or sigma; these defaults are a reading of it."""
     ny = nx if ny is None else ny
     X, Y = np.meshgrid(np.arange(nx) / (nx - 1), np.arange(ny) / (ny - 1))
     g = lambda yc: np.exp(-((X - x0) ** 2 + (Y - yc) ** 2) / (2.0 * sigma * sigma))
