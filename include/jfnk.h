@@ -279,6 +279,21 @@ jfnk_status jfnk_solve_batch(jfnk_ctx* ctx, int count, const jfnk_problem* probs
 jfnk_status jfnk_batch_stats(jfnk_ctx* ctx, long long* kernel_launches, int* tile_cells, int pde, int prec,
                              int nx, int ny);
 
+/* Tuning and diagnostic switches of a context; each call sets one knob.
+ *   JFNK_TUNE_BATCH_TILE: value > 0 fixes the batch engine's cells per tile
+ *     (rounded down to a multiple of 256, clamped to 256..2048) for every
+ *     problem class jfnk_solve_batch has not tuned yet on this context; 0
+ *     restores the measured choice per class. Results do not depend on it.
+ *   JFNK_TUNE_BULK_COPY: 1 (the default) lets the single-solve path stream the
+ *     Krylov basis through the bulk-copy ring; 0 restricts it to the plain-load
+ *     passes (classical Gram-Schmidt only: the delayed forms then return
+ *     JFNK_E_INVALID, as on grids the ring cannot take).
+ * JFNK_E_INVALID (nothing changes) for a NULL context, an unknown knob or a
+ * value outside its range. Call between solves: a solve in flight on another
+ * thread may see either setting. */
+typedef enum { JFNK_TUNE_BATCH_TILE = 0, JFNK_TUNE_BULK_COPY = 1 } jfnk_tune_knob;
+jfnk_status jfnk_tune(jfnk_ctx* ctx, int knob, long long value);
+
 /* Serving: queue a solve of `prob` (steps as in jfnk_solve) and return a
  * ticket at once. x0 and x_out are FP64 host or device arrays that must stay
  * valid until jfnk_poll returns a final status for the ticket. Requests are

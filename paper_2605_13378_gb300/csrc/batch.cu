@@ -458,12 +458,9 @@ int BatchEngine::tile_for(int pde, int ts, int tj, const jfnk_problem* prob, std
   const long long key = class_key(pde, pc, ncell);
   auto it = tiles_.find(key);
   if (it != tiles_.end()) return it->second;
-  const char* env = std::getenv("JFNK_BATCH_TILE");
-  if (env && std::atoi(env) > 0) {
-    int t = std::atoi(env);
-    t = std::max(kBatUnit, std::min(2048, (t / kBatUnit) * kBatUnit));
-    tiles_[key] = t;
-    return t;
+  if (tile_override_ > 0) {
+    tiles_[key] = tile_override_;
+    return tile_override_;
   }
   std::vector<int> cands;
   for (int c : kTileCands)

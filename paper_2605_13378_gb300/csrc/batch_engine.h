@@ -60,6 +60,8 @@ class BatchEngine {
   int tile_for(int pde, int ts, int tj, const jfnk_problem* prob, std::string* why);
   // The tile size chosen for a class so far (0: not tuned yet).
   int tuned_tile(int pde, int prec, long long ncell) const;
+  // Cells per tile for classes not tuned yet (0: measure per class).
+  void set_tile_override(int cells) { tile_override_ = cells; }
   void set_launches_per_replay(int l) { launches_ = l < 1 ? 1 : l; dirty_ = true; }
   int launches_per_replay() const { return launches_; }
   long long kernel_launches() const { return kernel_launches_; }
@@ -100,6 +102,7 @@ class BatchEngine {
   long long kernel_launches_ = 0;
   int graph_launches_ = 0;              // kernel launches in one replay
   std::map<long long, int> tiles_;      // autotuned cells per tile, by problem class
+  int tile_override_ = 0;               // fixed cells per tile for untuned classes (0: none)
 };
 
 }  // namespace jfnk

@@ -97,7 +97,8 @@ struct jfnk_ctx {
   double* dsc = nullptr;          // scalar slots
   unsigned int* derr = nullptr;   // device error word (bounded waits that expired)
   int nsm = 0;                    // multiprocessors: grid of the streaming kernels
-  bool stream_ok = true;          // bulk-copy streaming of the basis allowed (JFNK_NO_STREAM=1 disables)
+  bool stream_ok = true;          // bulk-copy streaming of the basis allowed (JFNK_TUNE_BULK_COPY)
+  int batch_tile = 0;             // JFNK_TUNE_BATCH_TILE: fixed cells per tile of the batch engine (0: measured)
   GmresCtl* gctl = nullptr;
   BicgCtl* bctl = nullptr;
   LsCtl* lsc = nullptr;           // line search of the current Newton step
@@ -896,8 +897,7 @@ static jfnk_status jfnk_create_impl(jfnk_ctx* ctx, int device, size_t hbm_budget
     return s;
   CK(cudaMemset(ctx->derr, 0, 256), "memset");
   CK(cudaDeviceGetAttribute(&ctx->nsm, cudaDevAttrMultiProcessorCount, device), "device attribute");
-  const char* ns = std::getenv("JFNK_NO_STREAM");
-  ctx->stream_ok = !(ns && ns[0] == '1');
+  ctx->stream_ok = true;
   CK(cudaMemset(ctx->dsc, 0, 64 * sizeof(double)), "memset");
   CK(cudaMemset(ctx->gctl, 0, sizeof(GmresCtl)), "memset");
   CK(cudaMemset(ctx->bctl, 0, sizeof(BicgCtl)), "memset");
@@ -1127,7 +1127,8 @@ static jfnk_status validate_opts(jfnk_ctx* ctx, const jfnk_opts* o) {
       return fail(ctx, JFNK_E_INVALID, "bad precond_damping");
   }
   if (o->krylov == JFNK_GMRES && o->ortho != JFNK_CGS2 && !(ctx->stream_ok && stream_supported(ctx->N)))
-    return fail(ctx, JFNK_E_INVALID, "delayed CGS2 needs the streaming kernels (unknowns a multiple of 8)");
+    return fail(ctx, JFNK_E_INVALID, "delayed CGS2 needs the bulk-copy streaming kernels (unknowns a multiple of 8, "
+                                     "JFNK_TUNE_BULK_COPY on)");
   if (o->krylov == JFNK_GMRES && o->ortho == JFNK_DCGS2_FUSED) {
     const bool ok = o->lin == JFNK_AD && tb == VT_F32 && tj == VT_F32 && ctx->stream_ok &&
                     dcgs_fused_supported(ctx->P, o->restart > 0 ? o->restart : kTuneMaxRestart, ctx->nsm);
@@ -1312,7 +1313,10 @@ jfnk_status jfnk_solve_batch(jfnk_ctx* ctx, int count, const jfnk_problem* probs
     return fail(ctx, JFNK_E_OOM, "batch workspace of " + std::to_string(need) + " bytes exceeds the HBM budget");
   CK(cudaSetDevice(ctx->device), "cudaSetDevice");
   CK(cudaStreamSynchronize(ctx->stream), "stream synchronize");   // caller's inputs are ready
-  if (!ctx->batch) ctx->batch = new jfnk::BatchEngine(ctx->device);
+  if (!ctx->batch) {
+    ctx->batch = new jfnk::BatchEngine(ctx->device);
+    ctx->batch->set_tile_override(ctx->batch_tile);
+  }
   jfnk::BatchEngine& E = *ctx->batch;
   std::string why;
   for (int i = 0; i < count; ++i) {
@@ -1363,6 +1367,25 @@ jfnk_status jfnk_solve_batch(jfnk_ctx* ctx, int count, const jfnk_problem* probs
     if (first == JFNK_OK && st[i] != JFNK_OK) first = st[i];
   }
   return first;
+}
+
+jfnk_status jfnk_tune(jfnk_ctx* ctx, int knob, long long value) {
+  if (!ctx) return JFNK_E_INVALID;
+  switch (knob) {
+    case JFNK_TUNE_BATCH_TILE: {
+      if (value < 0) return fail(ctx, JFNK_E_INVALID, "batch tile: cells must be >= 0");
+      const int t = value == 0 ? 0 : (int)std::max<long long>(256, std::min<long long>(2048, value / 256 * 256));
+      ctx->batch_tile = t;
+      if (ctx->batch) ctx->batch->set_tile_override(t);
+      return JFNK_OK;
+    }
+    case JFNK_TUNE_BULK_COPY:
+      if (value != 0 && value != 1) return fail(ctx, JFNK_E_INVALID, "bulk copy: 0 or 1");
+      ctx->stream_ok = value == 1;
+      return JFNK_OK;
+    default:
+      return fail(ctx, JFNK_E_INVALID, "unknown tuning knob");
+  }
 }
 
 jfnk_status jfnk_batch_stats(jfnk_ctx* ctx, long long* kernel_launches, int* tile_cells, int pde, int prec,

@@ -16,8 +16,7 @@ static double now_ms() {
 
 Server::Server(int device, size_t budget, int slots) : device_(device), budget_(budget) {
   if (slots < 1) slots = 1;
-  batch_max_cells_ = 1LL << 20;
-  if (const char* e = std::getenv("JFNK_SERVE_BATCH_MAX")) batch_max_cells_ = std::atoll(e);
+  batch_max_cells_ = 1LL << 20;   // unknowns (cells x fields) of the largest batched request
   for (int s = 0; s < slots; ++s) threads_.emplace_back(&Server::worker, this, s);
   threads_.emplace_back(&Server::batch_worker, this);
 }

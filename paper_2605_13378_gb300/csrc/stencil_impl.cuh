@@ -614,17 +614,10 @@ inline MarchGeom march_geom(const ProbDev& P, int vec) {
 
 static bool aligned(const void* p, size_t a) { return ((uintptr_t)p % a) == 0; }
 
-static int g_no_march = -1;   // JFNK_NO_MARCH=1 forces the gather form (testing both forms)
-
 template <class T, class TV>
 static bool march_ok(const ProbDev& P, const StencilArgs& a) {
   if (P.nf > 2) return false;   // four planes: the register rows would spill; the gather form serves them
   if (a.precond) return false;  // the preconditioned direction is formed per node in the gather form
-  if (g_no_march < 0) {
-    const char* e = getenv("JFNK_NO_MARCH");
-    g_no_march = (e && e[0] == '1') ? 1 : 0;
-  }
-  if (g_no_march) return false;
   const int vec = 16 / (int)sizeof(T);
   if (P.nx % vec != 0) return false;
   if (!aligned(a.x, 16)) return false;

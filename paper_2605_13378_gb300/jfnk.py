@@ -32,11 +32,12 @@ JFNK_FP64, JFNK_FP32, JFNK_MIXED_FP32, JFNK_MIXED_BF16 = 0, 1, 2, 3
 JFNK_EPS_SCALED, JFNK_EPS_PAPER = 0, 1
 JFNK_CGS2, JFNK_DCGS2, JFNK_DCGS2_FUSED = 0, 1, 2
 JFNK_MAX_RESTART = 64
+JFNK_TUNE_BATCH_TILE, JFNK_TUNE_BULK_COPY = 0, 1
 
 EXPORTED = ["jfnk_default_opts", "jfnk_create", "jfnk_set_problem", "jfnk_jvp", "jfnk_residual", "jfnk_solve",
             "jfnk_submit", "jfnk_poll", "jfnk_set_timing", "jfnk_kernel_stats", "jfnk_reset_stats",
             "jfnk_last_error", "jfnk_status_string", "jfnk_destroy", "jfnk_jvp_fd_noalloc", "jfnk_solve_batch",
-            "jfnk_batch_stats"]
+            "jfnk_batch_stats", "jfnk_tune"]
 
 
 class jfnk_problem(C.Structure):
@@ -86,6 +87,7 @@ _sigs = {
                                    C.POINTER(C.c_int), C.POINTER(jfnk_report), C.POINTER(C.c_int)]),
     "jfnk_batch_stats": (C.c_int, [_P, C.POINTER(C.c_longlong), C.POINTER(C.c_int), C.c_int, C.c_int, C.c_int,
                                    C.c_int]),
+    "jfnk_tune": (C.c_int, [_P, C.c_int, C.c_longlong]),
 }
 for _name, (_res, _args) in _sigs.items():
     _f = getattr(lib, _name)
@@ -220,6 +222,11 @@ def jfnk_batch_stats(ctx: int, pde: int = 0, prec: int = 0, nx: int = 0, ny: int
     tc = C.c_int()
     lib.jfnk_batch_stats(ctx, C.byref(kl), C.byref(tc), pde, prec, nx, ny)
     return kl.value, tc.value
+
+
+def jfnk_tune(ctx: int, knob: int, value: int) -> int:
+    """Set one tuning or diagnostic knob of a context (JFNK_TUNE_*; see include/jfnk.h)."""
+    return lib.jfnk_tune(ctx, knob, value)
 
 
 # --- small conveniences over the same calls ------------------------------------------------------

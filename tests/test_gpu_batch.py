@@ -11,7 +11,6 @@ Reductions are summed per 256-cell unit in a fixed order, so a problem's
 result must be bitwise the same in a batch of one and in the mix, whatever
 tile size the autotuner chose; that is checked with two forced tile sizes.
 """
-import os
 
 import numpy as np
 import pytest
@@ -112,21 +111,17 @@ def _band(run, x0, n_pert=4):
 
 
 def _batch(J, cases, tile=None):
-    if tile is not None:
-        os.environ["JFNK_BATCH_TILE"] = str(tile)
+    ctx = J.jfnk_create(0)
     try:
-        ctx = J.jfnk_create(0)
-        try:
-            xs = [torch.tensor(cs[3], device="cuda") for cs in cases]
-            s, reps, sts = J.jfnk_solve_batch(ctx, [cs[1] for cs in cases], [cs[2] for cs in cases], None, xs,
-                                              [cs[4] for cs in cases])
-            torch.cuda.synchronize()
-            return s, [x.cpu().numpy() for x in xs], reps, sts, J.jfnk_last_error(ctx)
-        finally:
-            J.jfnk_destroy(ctx)
-    finally:
         if tile is not None:
-            del os.environ["JFNK_BATCH_TILE"]
+            assert J.jfnk_tune(ctx, J.JFNK_TUNE_BATCH_TILE, tile) == J.JFNK_OK
+        xs = [torch.tensor(cs[3], device="cuda") for cs in cases]
+        s, reps, sts = J.jfnk_solve_batch(ctx, [cs[1] for cs in cases], [cs[2] for cs in cases], None, xs,
+                                          [cs[4] for cs in cases])
+        torch.cuda.synchronize()
+        return s, [x.cpu().numpy() for x in xs], reps, sts, J.jfnk_last_error(ctx)
+    finally:
+        J.jfnk_destroy(ctx)
 
 
 def test_mixed_batch_matches_oracle(J):

@@ -10,7 +10,6 @@ counts equal and Krylov counts within 2 per Newton step in FP64), and a
 problem's result is bitwise the same alone and in the mix at two forced tile
 sizes. Short restart lengths run the last dots pass of a cycle (no w) often.
 """
-import os
 
 import numpy as np
 import pytest
@@ -91,21 +90,17 @@ def _cases(J):
 
 
 def _batch(J, cases, tile=None):
-    if tile is not None:
-        os.environ["JFNK_BATCH_TILE"] = str(tile)
+    ctx = J.jfnk_create(0)
     try:
-        ctx = J.jfnk_create(0)
-        try:
-            xs = [torch.tensor(cs[3], device="cuda") for cs in cases]
-            s, reps, sts = J.jfnk_solve_batch(ctx, [cs[1] for cs in cases], [cs[2] for cs in cases], None, xs,
-                                              [cs[4] for cs in cases])
-            torch.cuda.synchronize()
-            return s, [x.cpu().numpy() for x in xs], reps, sts, J.jfnk_last_error(ctx)
-        finally:
-            J.jfnk_destroy(ctx)
-    finally:
         if tile is not None:
-            del os.environ["JFNK_BATCH_TILE"]
+            assert J.jfnk_tune(ctx, J.JFNK_TUNE_BATCH_TILE, tile) == J.JFNK_OK
+        xs = [torch.tensor(cs[3], device="cuda") for cs in cases]
+        s, reps, sts = J.jfnk_solve_batch(ctx, [cs[1] for cs in cases], [cs[2] for cs in cases], None, xs,
+                                          [cs[4] for cs in cases])
+        torch.cuda.synchronize()
+        return s, [x.cpu().numpy() for x in xs], reps, sts, J.jfnk_last_error(ctx)
+    finally:
+        J.jfnk_destroy(ctx)
 
 
 def test_dcgs2_batch_matches_oracle(J):

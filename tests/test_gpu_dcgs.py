@@ -185,6 +185,32 @@ def test_size_restriction_and_bicgstab_ignores_it(J, ctx):
     assert J.jfnk_solve(ctx, o, None, x, 1, None) == J.JFNK_E_INVALID
 
 
+def test_tune_knobs(J, ctx):
+    """jfnk_tune: an unknown knob or a value out of range is refused; with the bulk-copy ring off the delayed
+    form is refused and classical Gram-Schmidt on the plain-load passes gives the oracle's step."""
+    assert J.jfnk_tune(ctx, 9, 1) == J.JFNK_E_INVALID
+    assert J.jfnk_tune(ctx, J.JFNK_TUNE_BULK_COPY, 2) == J.JFNK_E_INVALID
+    assert J.jfnk_tune(ctx, J.JFNK_TUNE_BATCH_TILE, -1) == J.JFNK_E_INVALID
+    n = 96
+    lp = J.make_problem("allen_cahn", n, n, 0.1, 0.5, (1e-3, 1.0))
+    x0 = si.allen_cahn_ic(n, n, 3)
+    cgs2 = _opts(J, J.JFNK_FP64, ortho=J.JFNK_CGS2)
+    s, x_ring, _ = _run(J, ctx, lp, cgs2, x0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    assert J.jfnk_tune(ctx, J.JFNK_TUNE_BULK_COPY, 0) == J.JFNK_OK
+    s, _, _ = _run(J, ctx, lp, _opts(J, J.JFNK_FP64), x0, 1)
+    assert s == J.JFNK_E_INVALID and "bulk-copy" in J.jfnk_last_error(ctx)
+    s, x_plain, rep = _run(J, ctx, lp, cgs2, x0, 1)
+    assert s == J.JFNK_OK, J.jfnk_last_error(ctx)
+    p = opdes.AllenCahn2D(nx=n, ny=n, D=1e-3, dt=0.1, theta=0.5)
+    x_ref, reps = onw.time_steps(p, x0, 1, _oopts())
+    _compare(x_plain, x_ref, rep, reps, 1e-10)
+    assert np.abs(x_plain - x_ring).max() <= 1e-10 * np.abs(x_ring).max()
+    assert J.jfnk_tune(ctx, J.JFNK_TUNE_BULK_COPY, 1) == J.JFNK_OK
+    s, _, _ = _run(J, ctx, lp, _opts(J, J.JFNK_FP64), x0, 1)
+    assert s == J.JFNK_OK
+
+
 def test_allen_cahn_2048_step1_matches_stored_oracle_solve(J, ctx):
     """The benchmark grid in FP64 with delayed CGS2 against the oracle's stored (CGS2) solve at the same
     tolerances: the two Arnoldi forms are the same method, so the stored counts bind. The solution is compared
