@@ -27,11 +27,17 @@ constexpr int kDcgsBudget = 100 * 1024;   // largest entry: two entries always f
 constexpr int kDcgsMaxStages = 32;
 
 // bytes per vector of a super-chunk holding nv basis slots (+ the w chunk):
-// the largest power of two up to 32 KB whose entry fits the budget (larger
-// bulk copies stream faster; chunks shrink only as the basis grows)
+// the largest candidate up to 32 KB whose entry fits the budget (larger bulk
+// copies stream faster; chunks shrink only as the basis grows). The update
+// pass (pass 2) also takes 3 KB between 4 and 2 KB: there, fewer bulk copies
+// per byte paid off, while the dots pass streamed faster with 2 KB chunks and
+// a deeper ring. Every candidate is a multiple of 16 bytes (bulk-copy
+// granule), and the passes take any number of slices per chunk.
 template <class TB, class TJ>
-static int dcgs_scb(int nv, bool has_w, int* stage) {
-  for (int scb = 32768; scb >= 512; scb >>= 1) {
+static int dcgs_scb(int pass, int nv, bool has_w, int* stage) {
+  constexpr int kCand[] = {32768, 16384, 8192, 4096, 3072, 2048, 1024, 512};
+  for (int scb : kCand) {
+    if (scb == 3072 && pass != 2) continue;
     const int ce = scb / (int)sizeof(TB);
     int st = nv * scb + (has_w ? ce * (int)sizeof(TJ) : 0);
     st = (st + 127) / 128 * 128;
@@ -644,7 +650,7 @@ static cudaError_t dcgs_launch_k(int pass, long long n, void* V, int j, const vo
   typedef typename AccS<TJ>::type A;
   if (defer && (w == nullptr || red.max_blocks < 2 * nsm)) return cudaErrorInvalidValue;
   int stage = 0;
-  const int scb = dcgs_scb<TB, TJ>(j + 1, w != nullptr, &stage);
+  const int scb = dcgs_scb<TB, TJ>(pass, j + 1, w != nullptr, &stage);
   if (scb == 0) return cudaErrorInvalidValue;
   // as many ring entries (and their two barriers) as the per-block limit holds
   static SmemLimit limit_of[2];
