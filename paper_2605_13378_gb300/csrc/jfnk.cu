@@ -416,7 +416,7 @@ struct Solver {
       a.vscale = ctx->gctl->scale + j;
       a.out = w.w;
       a.active = &ctx->gctl->active;
-      a.pdl = pdl ? 1 : 0;
+      a.pdl = pdl ? 1 : 0;   // after the update pass (or a kernel launched plainly): neither writes x
       jfnk_status s = jvp(a, j);
       if (s) return s;
       const double bs = (double)(j + 1) * nv * sb();

@@ -95,7 +95,8 @@ struct JvpArgs {
   float* eps_out;              // FD: the step used (for reporting), may be null
   const int* active;           // device flag: the kernel does nothing when *active == 0 (null: always run)
   unsigned int* err;           // device error word for bounded waits of the staged sweep (null: not staged)
-  int pdl;                     // staged sweep: programmatic launch after the previous kernel in the stream
+  int pdl;                     // staged sweep: programmatic launch after the previous kernel in the stream,
+                               // which must not write x (the sweep loads x before its dependency wait)
   int precond;                 // the direction is M^-1 v (the problem's right preconditioner, gather form)
   double pbeta;                // its damping
 };

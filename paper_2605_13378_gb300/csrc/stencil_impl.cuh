@@ -54,7 +54,8 @@ struct StencilArgs {
   const int* active;
   LsCtl* ls;                // RESID: a line-search trial, alpha from ls->alpha (see LsCtl)
   unsigned int* err;        // AD, FD: device error word of the staged form's bounded waits (null: march form)
-  int pdl;                  // staged form: launched programmatically after the previous kernel
+  int pdl;                  // staged form: launched programmatically after the previous kernel, which
+                            // must not write x (the staged form starts loading x before its dependency wait)
   int precond;              // AD, FD: the direction is M^-1 v (PDE::precond at each node; gather form)
   double pbeta;             // damping beta of the preconditioner
 };

@@ -101,52 +101,92 @@ __device__ __forceinline__ StageUnit stage_unit(const StagePlan& g, int u, int n
   return s;
 }
 
+// Copy k < 6 NF of ring row rj of unit su into the slot at st: field k / 6;
+// x or v; the strip itself, its left or its right halo.
+template <class T, class TV, int NF, int POL>
+__device__ __forceinline__ void stage_copy(const ProbDev& P, const StagePlan& g, const StageUnit& su, int rj,
+                                           const T* x, const TV* v, unsigned char* st, uint64_t* bar, int k) {
+  constexpr int HX = 16 / (int)sizeof(T), HV = 16 / (int)sizeof(TV);
+  const int nx = P.nx;
+  const int f = k / 6, kind = k % 6;
+  const bool isv = kind >= 3;
+  const int part = kind % 3;
+  const int H = isv ? HV : HX;
+  const int es = isv ? (int)sizeof(TV) : (int)sizeof(T);
+  const int Wrow = g.W + 2 * H;
+  const char* base = isv ? (const char*)(v + (size_t)f * P.ncell + (size_t)rj * nx)
+                         : (const char*)(x + (size_t)f * P.ncell + (size_t)rj * nx);
+  unsigned char* dst = st + (isv ? g.offv : 0) + (size_t)f * Wrow * es;
+  int c0, cnt, dpos;
+  if (part == 0) {
+    c0 = su.col0; cnt = su.Wu; dpos = H;
+  } else if (part == 1) {   // the H columns before the strip
+    c0 = su.col0 >= H ? su.col0 - H : (POL == BP_WRAP ? nx - H : 0);
+    cnt = H; dpos = 0;
+  } else {                  // the H columns after it
+    c0 = su.col0 + su.Wu < nx ? su.col0 + su.Wu : (POL == BP_WRAP ? 0 : nx - H);
+    cnt = H; dpos = H + su.Wu;
+  }
+  bulk_g2s(dst + (size_t)dpos * es, base + (size_t)c0 * es, (uint32_t)(cnt * es), bar);
+}
+
+// Before the grid dependency wait: the x copies of the first rows of the CTA's
+// first unit su (as many as the empty ring holds; row q goes to slot q), with
+// their bytes added to each slot's transaction count but no arrival, so no
+// slot completes before stage_produce_unit adds the v copies and arrives.
+// Returns the number of rows started.
+template <class T, class TV, int NF, int POL>
+__device__ __forceinline__ int stage_prefetch_x(const ProbDev& P, const StagePlan& g, const StageUnit& su,
+                                                const T* x, unsigned char* sring, uint64_t* full) {
+  constexpr int HX = 16 / (int)sizeof(T);
+  const int lane = threadIdx.x & 31;
+  const int rows = su.j1 - su.j0 + 2;
+  const int pre = rows < g.slots ? rows : g.slots;
+  const uint32_t xb = (uint32_t)NF * (su.Wu + 2 * HX) * (uint32_t)sizeof(T);
+  for (int q = 0; q < pre; ++q) {
+    const int rj = bp_index(su.j0 - 1 + q, P.ny, POL);
+    if (lane == 0) mbar_expect_tx(&full[q], xb);
+    __syncwarp();
+    if (lane < 3 * NF)
+      stage_copy<T, TV, NF, POL>(P, g, su, rj, x, (const TV*)nullptr, sring + (size_t)q * g.slot_bytes, &full[q],
+                                 (lane / 3) * 6 + lane % 3);
+    __syncwarp();
+  }
+  return pre;
+}
+
 // Producer: rows j0 - 1 .. j1 of unit u (wrapped or clamped in y) into the
-// ring, row counter q continuing across units. Lane k < 6 NF issues copy k:
-// field k / 6; x or v; the strip itself, its left or its right halo.
+// ring, row counter q continuing across units. Lane k < 6 NF issues copy k
+// (stage_copy). The first xdone rows (the CTA's first unit only) had their x
+// copies started by stage_prefetch_x: they take the v copies and the arrival,
+// whatever the abort flag says, so that every started slot completes.
 template <class T, class TV, int NF, int POL>
 __device__ __forceinline__ bool stage_produce_unit(const ProbDev& P, const StagePlan& g, const StageUnit& su,
                                                    const T* x, const TV* v, unsigned char* sring, uint64_t* full,
                                                    uint64_t* empty, RingPos* pos, int* filled, unsigned int* err,
-                                                   int* s_abort) {
+                                                   int* s_abort, int xdone) {
   constexpr int HX = 16 / (int)sizeof(T), HV = 16 / (int)sizeof(TV);
   const int lane = threadIdx.x & 31;
-  const int nx = P.nx;
-  const uint32_t bytes = (uint32_t)NF * ((su.Wu + 2 * HX) * (uint32_t)sizeof(T) + (su.Wu + 2 * HV) * (uint32_t)sizeof(TV));
-  for (int r = su.j0 - 1; r <= su.j1; ++r, pos->next(g.slots), ++*filled) {
+  const uint32_t xb = (uint32_t)NF * (su.Wu + 2 * HX) * (uint32_t)sizeof(T);
+  const uint32_t vb = (uint32_t)NF * (su.Wu + 2 * HV) * (uint32_t)sizeof(TV);
+  int q = 0;
+  for (int r = su.j0 - 1; r <= su.j1; ++r, ++q, pos->next(g.slots), ++*filled) {
     const int slot = pos->slot;
-    // a slot's k-th refill waits for the k-th release (empty phase k - 1)
-    if (*filled >= g.slots && !mbar_wait_bounded(&empty[slot], pos->phase ^ 1u, kWaitLimitNs)) {
-      if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); *s_abort = 1; }
-      return false;
+    const bool started = q < xdone;
+    if (!started) {
+      // a slot's k-th refill waits for the k-th release (empty phase k - 1)
+      if (*filled >= g.slots && !mbar_wait_bounded(&empty[slot], pos->phase ^ 1u, kWaitLimitNs)) {
+        if (lane == 0) { atomicExch(err, (unsigned)STREAM_TIMEOUT); *s_abort = 1; }
+        return false;
+      }
+      if (*s_abort) return false;
     }
-    if (*s_abort) return false;
     const int rj = bp_index(r, P.ny, POL);
     unsigned char* st = sring + (size_t)slot * g.slot_bytes;
-    if (lane == 0) mbar_arrive_expect_tx(&full[slot], bytes);
+    if (lane == 0) mbar_arrive_expect_tx(&full[slot], started ? vb : xb + vb);
     __syncwarp();
-    if (lane < 6 * NF) {
-      const int f = lane / 6, kind = lane % 6;
-      const bool isv = kind >= 3;
-      const int part = kind % 3;
-      const int H = isv ? HV : HX;
-      const int es = isv ? (int)sizeof(TV) : (int)sizeof(T);
-      const int Wrow = g.W + 2 * H;
-      const char* base = isv ? (const char*)(v + (size_t)f * P.ncell + (size_t)rj * nx)
-                             : (const char*)(x + (size_t)f * P.ncell + (size_t)rj * nx);
-      unsigned char* dst = st + (isv ? g.offv : 0) + (size_t)f * Wrow * es;
-      int c0, cnt, dpos;
-      if (part == 0) {
-        c0 = su.col0; cnt = su.Wu; dpos = H;
-      } else if (part == 1) {   // the H columns before the strip
-        c0 = su.col0 >= H ? su.col0 - H : (POL == BP_WRAP ? nx - H : 0);
-        cnt = H; dpos = 0;
-      } else {                  // the H columns after it
-        c0 = su.col0 + su.Wu < nx ? su.col0 + su.Wu : (POL == BP_WRAP ? 0 : nx - H);
-        cnt = H; dpos = H + su.Wu;
-      }
-      bulk_g2s(dst + (size_t)dpos * es, base + (size_t)c0 * es, (uint32_t)(cnt * es), &full[slot]);
-    }
+    if (lane < 6 * NF && (!started || lane % 6 >= 3))
+      stage_copy<T, TV, NF, POL>(P, g, su, rj, x, v, st, &full[slot], lane);
     __syncwarp();
   }
   return true;
@@ -193,15 +233,13 @@ __global__ void __launch_bounds__(kStageThreads, 3)
   constexpr int POL = PDE::POLICY;
   constexpr int VEC = 16 / (int)sizeof(T);
   constexpr int HX = 16 / (int)sizeof(T), HV = 16 / (int)sizeof(TV);
-  grid_dep_wait();      // the kernel that wrote v (and the active flag) has completed (programmatic launch)
-  grid_dep_trigger();
-  if (a.active && *a.active == 0) return;
   unsigned int* err = a.err;
   extern __shared__ __align__(128) unsigned char sring[];
   uint64_t* full = (uint64_t*)(sring + (size_t)g.slots * g.slot_bytes);
   uint64_t* empty = full + g.slots;
   __shared__ int s_abort;
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int nx = P.nx, ny = P.ny;
   if (tid == 0) {
     for (int q = 0; q < g.slots; ++q) {
       mbar_init(&full[q], 1);
@@ -210,18 +248,36 @@ __global__ void __launch_bounds__(kStageThreads, 3)
     fence_mbar_init();
     s_abort = 0;
   }
+  __syncthreads();
+  // Launched programmatically, the sweep follows a kernel that does not write
+  // the state x (the update pass of a delayed-CGS2 step writes only the basis),
+  // so the producer starts the x rows of its first unit while that kernel
+  // finishes; v, the scale and the active flag are read after the wait. A
+  // plain launch has nothing to overlap and fills its rows in one pass.
+  int xpre = 0;
+  if (warp == 0 && a.pdl)
+    xpre = stage_prefetch_x<T, TV, NF, POL>(P, g, stage_unit(g, blockIdx.x, nx, ny), (const T*)a.x, sring, full);
+  grid_dep_wait();      // the kernel that wrote v (and the active flag) has completed (programmatic launch)
+  grid_dep_trigger();
+  if (a.active && *a.active == 0) {
+    // nothing to compute: complete the started slots and let their copies land before the CTA exits
+    if (warp == 0 && lane == 0) {
+      for (int q = 0; q < xpre; ++q) mbar_arrive(&full[q]);
+      const uint64_t deadline = global_timer_ns() + kWaitLimitNs;
+      for (int q = 0; q < xpre; ++q) mbar_wait_until(&full[q], 0u, deadline);
+    }
+    return;
+  }
   const T s = a.vscale ? T(*a.vscale) : T(1);
   const T eps = fd_step<T, MODE>(a, s);
-  __syncthreads();
   const CB cb = make_comb<MODE, T>(0.0, s, eps);
-  const int nx = P.nx, ny = P.ny;
   if (warp == 0) {
     RingPos pos{0, 0u};
     int filled = 0;
     for (int u = blockIdx.x; u < g.units; u += gridDim.x) {
       const StageUnit su = stage_unit(g, u, nx, ny);
       if (!stage_produce_unit<T, TV, NF, POL>(P, g, su, (const T*)a.x, (const TV*)a.v, sring, full, empty, &pos,
-                                               &filled, err, &s_abort))
+                                               &filled, err, &s_abort, u == (int)blockIdx.x ? xpre : 0))
         break;
     }
     if (s_abort && lane == 0) {   // drain the copies still in flight before the CTA exits
