@@ -36,7 +36,9 @@
 extern "C" {
 #endif
 
-#define JFNK_ABI_VERSION 2
+/* Raised when an entry point, a struct layout or a documented behaviour of
+ * this header changes (3: jfnk_tune; the library reads no environment). */
+#define JFNK_ABI_VERSION 3
 #define JFNK_MAX_RESTART 64   /* largest GMRES restart length m */
 
 typedef struct jfnk_ctx jfnk_ctx;

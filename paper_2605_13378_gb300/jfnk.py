@@ -32,6 +32,9 @@ JFNK_FP64, JFNK_FP32, JFNK_MIXED_FP32, JFNK_MIXED_BF16 = 0, 1, 2, 3
 JFNK_EPS_SCALED, JFNK_EPS_PAPER = 0, 1
 JFNK_CGS2, JFNK_DCGS2, JFNK_DCGS2_FUSED = 0, 1, 2
 JFNK_MAX_RESTART = 64
+JFNK_ABI_VERSION = 3
+JFNK_NOALLOC_MAX_FX_BYTES = 4194304
+JFNK_NOALLOC_SCRATCH_BYTES = 4352 + JFNK_NOALLOC_MAX_FX_BYTES
 JFNK_TUNE_BATCH_TILE, JFNK_TUNE_BULK_COPY = 0, 1
 
 EXPORTED = ["jfnk_default_opts", "jfnk_create", "jfnk_set_problem", "jfnk_jvp", "jfnk_residual", "jfnk_solve",

@@ -46,6 +46,24 @@ def test_struct_layouts_match_the_header(lib, tmp_path):
     assert sizes == [ctypes.sizeof(lib.jfnk_problem), ctypes.sizeof(lib.jfnk_opts), ctypes.sizeof(lib.jfnk_report)]
 
 
+def test_constants_match_the_header(lib, tmp_path):
+    """Every JFNK_* enumerator and numeric #define of the header has the same value in the binding."""
+    txt = open(HEADER).read()
+    names = sorted(set(re.findall(r"\b(JFNK_[A-Z0-9_]+)\s*=", txt))
+                   | {n for n in re.findall(r"#define\s+(JFNK_[A-Z0-9_]+)\s+\S", txt) if n != "JFNK_H"})
+    assert len(names) > 30
+    body = "".join(f'printf("{n} %lld\\n", (long long)({n}));' for n in names)
+    src = tmp_path / "consts.c"
+    src.write_text('#include <stdio.h>\n#include "jfnk.h"\nint main(void){' + body + "return 0;}\n")
+    exe = tmp_path / "consts"
+    subprocess.run(["gcc", "-I" + os.path.dirname(HEADER), str(src), "-o", str(exe)], check=True)
+    out = subprocess.run([str(exe)], capture_output=True, text=True, check=True).stdout.split("\n")
+    vals = dict((ln.split()[0], int(ln.split()[1])) for ln in out if ln)
+    assert set(vals) == set(names)
+    for n, v in vals.items():
+        assert getattr(lib, n) == v, n
+
+
 def test_host_only_entry_points(lib):
     o = lib.jfnk_default_opts(lib.JFNK_FP64)
     assert (o.tol_newton, o.tol_krylov, o.max_newton, o.max_krylov) == (1e-6, 1e-8, 15, 100)
@@ -56,6 +74,7 @@ def test_host_only_entry_points(lib):
     assert lib.lib.jfnk_create(None, 0, 0, None) == lib.JFNK_E_INVALID
     assert lib.lib.jfnk_set_problem(None, None) == lib.JFNK_E_INVALID
     assert lib.lib.jfnk_solve(None, None, None, None, 1, None) == lib.JFNK_E_INVALID
+    assert lib.jfnk_tune(None, lib.JFNK_TUNE_BATCH_TILE, 512) == lib.JFNK_E_INVALID
 
 
 def test_no_cpu_fallback_in_the_product():
